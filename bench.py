@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the m=0 laser-envelope PIC timestep on GB300.
+
+One "step" is one full timestep of the hot path (Faraday, gather + chi deposit + ponderomotive
+Boris, envelope solve, position push + charge-conserving current, Ampere, moving window with
+injection, periodic counting sort) on the 2048 x 256-cell, 8,388,608-electron workload, with
+every input resident in HBM.  The headline value is FP32_MIXED particle-steps/s; the FP64
+path is timed beside it on the same workload, and the FP32-vs-FP64 errors of the on-axis wake
+and of peak |A| are reported with them.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one per GPU; the method's single-simulation
+path has no collective).  `--impl reference` times the FP64 CPU oracle on the host cores on the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import C2  # noqa: E402
+
+WORKLOAD = C2
+# Algorithmic bytes per particle of each particle kernel and per grid node of each grid
+# kernel, by precision (read + write of the arrays the kernel must touch once).
+PARTICLE_BYTES = {
+    "fp32": {"pass_a": 32 + 12, "pass_b": 32 + 16},
+    "fp64": {"pass_a": 60 + 24, "pass_b": 60 + 32},
+}
+
+
+def node_bytes(prec: str) -> dict:
+    r = 4 if prec == "fp32" else 8
+    return {
+        # read ex, er, bt, A; write bt, btn, phi, gx, gr; clear chi, jx, jr (FP64)
+        "prepass": 3 * r + 2 * r + 5 * r + 3 * 8,
+        # read A^n, A^{n-1}, chi; write A^{n+1}, phih
+        "envelope": 2 * r + 2 * r + 8 + 2 * r + r,
+        # read bt, jr, jx, er, ex; write er, ex
+        "ampere": 3 * r + 2 * 8 + 2 * r,
+    }
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def source_sha(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "pass_a": ["paper_1912_04674_gb300/csrc/particles.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
+    "pass_b": ["paper_1912_04674_gb300/csrc/particles.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
+    "prepass": ["paper_1912_04674_gb300/csrc/fields.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
+    "envelope": ["paper_1912_04674_gb300/csrc/fields.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
+    "ampere": ["paper_1912_04674_gb300/csrc/fields.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
+}
+
+
+def traffic_from_profile(kernel: str, prec: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path)).get(f"{kernel}:{prec}")
+    except Exception:
+        return None
+    if not t or t.get("source_sha") != source_sha(KERNEL_SOURCES.get(kernel, [])):
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.stop_ev = gpu, [], threading.Event()
+        self.t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([v.strip() for v in out.split(",")])
+            except Exception:
+                return
+            self.stop_ev.wait(0.2)
+
+    def __enter__(self):
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop_ev.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        smax = max((float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------- our arm
+def make_sim(prec: str, w=WORKLOAD):
+    from paper_1912_04674_gb300 import lpic as L
+    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every)
+    return L.Simulation(g, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
+                        L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), precision=prec)
+
+
+def timed_steps(sim, k: int):
+    """Device time of k steps on the library's stream (CUDA events), alive counts around it."""
+    import torch
+    a0 = sim.counters()["alive"]
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = sim.stream
+    torch.cuda.synchronize()
+    s.record(st)
+    sim.step(k)
+    e.record(st)
+    torch.cuda.synchronize()
+    a1 = sim.counters()["alive"]
+    return s.elapsed_time(e), 0.5 * (a0 + a1)
+
+
+def kernel_profile(sim, k: int):
+    sim.set_timing(True)
+    sim.kernel_stats()
+    before = {n: v[0] for n, v in sim.kernel_stats().items()}
+    sim.step(k)
+    stats = sim.kernel_stats()
+    sim.set_timing(False)
+    out = {}
+    for n, (launches, ms) in stats.items():
+        dl = launches - before.get(n, 0)
+        if dl > 0:
+            out[n] = {"launches": dl, "ms_total": ms, "ms_avg": ms / dl}
+    return out
+
+
+def roofline(prof: dict, prec: str, alive: float, pk: dict):
+    nodes = (WORKLOAD.nx + 1) * (WORKLOAD.nr + 1)
+    nb = node_bytes(prec)
+    dominant = max(prof, key=lambda n: prof[n]["ms_total"])
+    if dominant in PARTICLE_BYTES[prec]:
+        bytes_ = PARTICLE_BYTES[prec][dominant] * alive
+    else:
+        bytes_ = nb.get(dominant, 0) * nodes
+    t = prof[dominant]["ms_avg"] * 1e-3
+    peak = pk.get("hbm_gbs")
+    ach = bytes_ / t / 1e9
+    share = prof[dominant]["ms_total"] / sum(v["ms_total"] for v in prof.values())
+    return {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4) if peak else None,
+            "traffic": traffic_from_profile(dominant, prec), "algorithmic_bytes": int(bytes_),
+            "ms_per_launch": round(prof[dominant]["ms_avg"], 4), "share_of_step": round(share, 3),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak else "none"}
+
+
+def e2e_run(prec: str, k: int):
+    """Same metric through the public API with host buffers: upload of the initial state from
+    pinned host memory, then k steps each followed by a read of the on-axis wake."""
+    import numpy as np
+    import torch
+    sim = make_sim(prec)
+    parts = sim.particles()
+    fields = {n: sim.field(n) for n in ("ex", "er", "bt", "a", "am")}
+    pin = {n: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for n, v in parts.items()}
+    pinf = {n: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for n, v in fields.items()}
+    h2d = sum(v.nbytes for v in pin.values()) + sum(v.nbytes for v in pinf.values())
+    alive = len(parts["x"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n, v in pinf.items():
+        sim.upload_field(n, v)
+    sim.upload_particles(pin)
+    d2h = 0
+    for _ in range(k):
+        sim.step(1)
+        d2h += sim.ex_axis().nbytes
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": alive * k / dt, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d / k),
+            "d2h_bytes_per_step": int(d2h / k), "steps": k,
+            "note": "initial-state upload amortised over the steps; wake read back every step"}
+
+
+def accuracy(k_total: int):
+    """FP32_MIXED vs FP64 on the same workload after k_total steps."""
+    import numpy as np
+    s64, s32 = make_sim("fp64"), make_sim("fp32")
+    s64.step(k_total)
+    s32.step(k_total)
+    e64, e32 = s64.ex_axis(), s32.ex_axis()
+    a64, a32 = s64.a_abs_max(), s32.a_abs_max()
+    out = {"steps": k_total,
+           "wake_ex_rel_l2": float(np.linalg.norm(e32 - e64) / max(np.linalg.norm(e64), 1e-300)),
+           "a_max_rel": float(abs(a32 - a64) / a64)}
+    s64.close()
+    s32.close()
+    return out
+
+
+def cpu_baseline(max_seconds=20.0):
+    from oracle.oracle import OSim
+    w = WORKLOAD
+    o = OSim(w.nx, w.nr, w.dx, w.dr, w.dt, True)
+    o.init_envelope(w.a0, w.w0, w.L, w.x_center, w.x_center)
+    o.load_plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed)
+    steps, units, t0 = 0, 0.0, time.perf_counter()
+    while steps < 1 or time.perf_counter() - t0 < max_seconds:
+        n = o.np
+        o.step(1)
+        steps += 1
+        units += n
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{w.name}: first {steps} timesteps of the FP64 oracle, single thread "
+                      f"({units:.3g} particle-steps, {dt:.1f} s)"}
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    pk = peaks()
+    result = {}
+    for prec, k in (("fp32", args.steps), ("fp64", max(3, args.steps // 8))):
+        sim = make_sim(prec)
+        sim.step(args.warmup)
+        launches0 = sum(v[0] for v in sim.kernel_stats().values())
+        barrier()
+        with ClockSampler(local) as cs:
+            ms, alive = timed_steps(sim, k)
+        barrier()
+        launches = sum(v[0] for v in sim.kernel_stats().values()) - launches0
+        ms_max = max_over_ranks(ms)
+        units = sum_over_ranks(alive * k)
+        prof = kernel_profile(sim, max(3, min(k, 40)))
+        result[prec] = {"value": units / (ms_max * 1e-3), "ms_per_step": ms_max / k, "steps": k,
+                        "alive": alive, "gpu_launches": launches, "clocks": cs.summary(),
+                        "roofline": roofline(prof, prec, alive, pk),
+                        "kernels": {n: round(v["ms_avg"], 4) for n, v in prof.items()}}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+
+    acc = accuracy(args.warmup + result["fp64"]["steps"]) if rank == 0 else None
+    e2e = e2e_run("fp32", args.steps) if rank == 0 else None
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if rank == 0:
+        r32, r64 = result["fp32"], result["fp64"]
+        w = WORKLOAD
+        line = {
+            "metric": "particle-steps/s FP32 vs FP64 at <=1e-3 wake err; scan p50/p99 latency",
+            "value": r32["value"], "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "nr": w.nr, "particles": w.particles,
+                       "ppc": list(w.ppc), "a0": w.a0, "w0": w.w0, "L": w.L, "n0": w.n0,
+                       "ramp_cells": w.ramp_cells, "sort_every": w.sort_every,
+                       "precision": "fp32_mixed (FP32 push/gather/stencils, FP64 axis rows and J/chi accumulation)",
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (particle arrays 2 x 336 MB FP32, 1.1 GB FP64)"},
+            "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
+                     "roofline": r64["roofline"], "gpu_launches": r64["gpu_launches"],
+                     "clocks": r64["clocks"]},
+            "fp32_vs_fp64": acc,
+            "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
+            "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r32["gpu_launches"],
+            "clocks": r32["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.oracle import OSim
+    w = WORKLOAD
+    o = OSim(w.nx, w.nr, w.dx, w.dr, w.dt, True)
+    o.init_envelope(w.a0, w.w0, w.L, w.x_center, w.x_center)
+    o.load_plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed)
+    budget = 150.0  # seconds of timed oracle work at most
+    t_start = time.perf_counter()
+    for _ in range(args.warmup):
+        if time.perf_counter() - t_start > 30.0:
+            break
+        o.step(1)
+    steps, units, t0 = 0, 0.0, time.perf_counter()
+    while steps < args.steps and (steps < 1 or time.perf_counter() - t0 < budget):
+        n = o.np
+        o.step(1)
+        steps += 1
+        units += n
+    dt = time.perf_counter() - t0
+    v = units / dt
+    sample = f"{w.name}: {steps} of {args.steps} requested FP64 oracle timesteps (150 s cap), single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": "particle-steps/s FP32 vs FP64 at <=1e-3 wake err; scan p50/p99 latency",
+        "value": v, "unit": "particle-steps/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "nr": w.nr, "particles": w.particles},
+        "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    from paper_1912_04674_gb300 import build
+    build.build()
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * lpic.h -- C ABI of the GB300 (sm_103a) implementation of one timestep of the
+ * cylindrical (azimuthal mode m=0) laser-envelope particle-in-cell method of
+ * Massimo et al., arXiv:1912.04674.
+ *
+ * Normalised units throughout (paper Sec. 2): lengths in c/w0, time in 1/w0,
+ * fields in m c w0/e, densities in n_c.  Macro-particles are electrons
+ * (q = -1, m = 1) over an immobile neutralising ion background.
+ *
+ * Memory and streams.  The caller owns ONE device buffer of
+ * lpic_required_bytes() bytes and the CUDA stream; the library sub-allocates
+ * every grid, particle and scratch array from that buffer and never calls
+ * cudaMalloc.  Every call that launches work enqueues it on the context's
+ * stream and returns without synchronising, except lpic_diagnose and
+ * lpic_upload, which synchronise that stream.  The caller must not touch the
+ * buffer while work is in flight.  A context is used by one host thread at a
+ * time.
+ *
+ * Errors.  Every call returns an lpic_status; nothing is thrown across the ABI.
+ * lpic_last_error() gives a message for the last failing call on a context.
+ * Errors found on the device (particle capacity exhausted, a non-finite value)
+ * are latched in the context and reported by the next call.
+ *
+ * Canonical grid layout used by dumps and uploads: [i][j], radial index j
+ * fastest, FP64 (complex values as (re, im) pairs), with the staggering
+ *   A, chi, Phi, dq : (i, j)        i in [0,Nx], j in [0,Nr]   (Nx+1) x (Nr+1)
+ *   Ex, Jx          : (i+1/2, j)    i in [0,Nx-1], j in [0,Nr] Nx x (Nr+1)
+ *   Er, Jr          : (i, j+1/2)    i in [0,Nx], j in [0,Nr-1] (Nx+1) x Nr
+ *   Bt              : (i+1/2, j+1/2)                           Nx x Nr
+ * (paper Sec. 3: Yee-like cell with Lifschitz centring, envelope centred like E).
+ */
+#ifndef LPIC_H
+#define LPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lpic_ctx lpic_ctx;
+typedef struct lpic_batch lpic_batch;
+
+typedef enum {
+    LPIC_OK = 0,
+    LPIC_EINVAL = 1,         /* bad argument or size                                   */
+    LPIC_ECFL = 2,           /* time step outside the stability region of a solver    */
+    LPIC_ENOMEM_BUDGET = 3,  /* caller buffer smaller than lpic_required_bytes        */
+    LPIC_EBUFSIZE = 4,       /* output buffer too small, or particle capacity exceeded */
+    LPIC_ECUDA = 5,          /* a CUDA runtime call failed                             */
+    LPIC_ETIMEOUT = 6,       /* a bounded device wait gave up                          */
+    LPIC_ENONFINITE = 7,     /* a NaN/Inf was found by a diagnostic                    */
+    LPIC_ESTATE = 8          /* call out of order (e.g. step before init)              */
+} lpic_status;
+
+typedef enum {
+    LPIC_FP64 = 0,           /* everything in FP64                                        */
+    LPIC_FP32_MIXED = 1      /* FP32 push/gather/stencils, int cell + FP32 offset
+                                positions, FP64 axis rows and FP64 J/chi accumulation      */
+} lpic_precision;
+
+/* Grid and time step (paper Sec. 3; benchmarks of Sec. 4 use dt = 0.8 dx or 0.9 dx). */
+typedef struct {
+    int32_t nx, nr;              /* cells in x and r; r_max = nr*dr; Nx*Nr < 2^31           */
+    double dx, dr, dt;           /* must satisfy the stability limits of lpic_check_params  */
+    int32_t moving_window;       /* 1: window moves at c (shift one cell when (n+1)dt >= (s+1)dx) */
+    int32_t sort_every;          /* counting sort + compaction of particles every k steps (>=1) */
+    int64_t particle_capacity;   /* particle slots; lpic_particle_capacity() gives a value  */
+    int32_t track_continuity;    /* 1: also deposit the per-step charge change (diagnostic) */
+    double accel_px_min;         /* p_x threshold of "accelerated" electrons; <= 0 means 10 */
+} lpic_grid_params;
+
+/* Gaussian envelope (paper Sec. 4; paraxial focused pulse, field profile exp(-xi^2/L^2)). */
+typedef struct {
+    double a0, w0, L;            /* peak |A|, waist, 1/e field half-length                  */
+    double x_center, x_focus;    /* lab-frame pulse centre at t=0 and focal plane           */
+} lpic_laser_params;
+
+/* Plasma: density n0 (n_c), zero before x_start, linear up-ramp of length ramp_len;
+ * regular lattice of ppc_x * ppc_r * ppc_theta particles per (x, r) cell (paper Sec. 4
+ * uses 6 per cell; the build's workloads 2x2x4), azimuthal offset from SplitMix64(seed). */
+typedef struct {
+    double n0, x_start, ramp_len;
+    int32_t ppc_x, ppc_r, ppc_theta;
+    uint64_t seed;
+} lpic_plasma_params;
+
+typedef enum {
+    LPIC_DIAG_EX_AXIS = 0,       /* Nx doubles: Ex(i+1/2, r=0) (paper Sec. 4, on-axis wake)  */
+    LPIC_DIAG_A_ABS_MAX = 1,     /* 1 double: max |A| over the grid                          */
+    LPIC_DIAG_WAIST = 2,         /* 1 double: sqrt(2 <r^2>) weighted by |A|^2 (Sec. 4, w(x)) */
+    LPIC_DIAG_CONT_RESIDUAL = 3, /* 1 double: max_ij |dQ/dt + div I| / max_ij |div I| over
+                                    interior nodes for the last step (needs track_continuity) */
+    LPIC_DIAG_ACCEL_ENERGY = 4,  /* 4 doubles: count, sum w, weighted mean and rms of gamma-1
+                                    over alive electrons with p_x > accel_px_min            */
+    LPIC_DIAG_COUNTERS = 5,      /* 4 int64: step n, window shift s, particle slots, alive   */
+    LPIC_DIAG_EX = 10, LPIC_DIAG_ER = 11, LPIC_DIAG_BT = 12,
+    LPIC_DIAG_A = 13,            /* A^n, complex (re,im)                                     */
+    LPIC_DIAG_AM = 14,           /* A^{n-1}, complex (re,im)                                 */
+    LPIC_DIAG_CHI = 15, LPIC_DIAG_JX = 16, LPIC_DIAG_JR = 17, LPIC_DIAG_DQ = 18,
+    LPIC_DIAG_PARTICLES = 20,    /* 7 x n doubles, SoA: x(lab), y, z, px, py, pz, w          */
+    LPIC_DIAG_PARTICLE_IDS = 21  /* n uint64 ids, same order as LPIC_DIAG_PARTICLES          */
+} lpic_diag_kind;
+
+/* Stability and consistency check of the parameters, host only (needs no GPU).
+ * Limits (dt, dx, dr):
+ *   Yee m=0:   dt * sqrt(4/dx^2 + 4.842/dr^2) < 2      (4.842/dr^2: spectral radius of
+ *              the discrete radial operator including the axis row)
+ *   envelope:  dt^2 [(2 + 2 sqrt(1+dx^2))/dx^2 + 4.842/dr^2] <= 2 + 2 sqrt(1+dt^2)
+ *              dt^2 (2 sqrt(1+dx^2) - 2)/dx^2              <= 2 sqrt(1+dt^2) - 2
+ *              (roots of the centred scheme of Eq. envelope_solver on the unit circle)
+ *   particles: dt < dx and dt < dr (a particle moves less than one cell per step)
+ * Returns LPIC_OK, LPIC_EINVAL or LPIC_ECFL; writes a message into msg (may be NULL). */
+lpic_status lpic_check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
+                              char *msg, size_t msg_cap);
+
+/* Particle slots needed for plasma p on grid g: the full window plus the injection of
+ * (sort_every + 2) window shifts between compactions.  0 for p == NULL. */
+int64_t lpic_particle_capacity(const lpic_grid_params *g, const lpic_plasma_params *p);
+
+/* Bytes of the caller-owned device buffer for grid g (with g->particle_capacity) in
+ * precision prec; 0 if the parameters are invalid. */
+size_t lpic_required_bytes(const lpic_grid_params *g, lpic_precision prec);
+
+/* Create a context on the current CUDA device (paper Sec. 3: the 2D (x,r) grid).
+ * device_buf: caller-owned, >= lpic_required_bytes(g, prec) bytes, 256-byte aligned,
+ * must stay valid until lpic_destroy.  cuda_stream: a cudaStream_t (NULL = default).
+ * Zeroes all fields; no particles.  *out is set only on LPIC_OK. */
+lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_precision prec,
+                           void *device_buf, size_t buf_bytes, void *cuda_stream);
+
+/* Write the Gaussian envelope A^0 (t=0) and A^{-1} (t=-dt) on the current window
+ * (paper Sec. 4 benchmarks; paraxial focused Gaussian, xR = w0^2/2). */
+lpic_status lpic_init_envelope(lpic_ctx *ctx, const lpic_laser_params *laser);
+
+/* Load the plasma lattice on every cell column of the current window and remember the
+ * profile for injection at the moving-window front (paper Sec. 4: uniform plasma,
+ * regular particles per cell).  Cold (p = 0).  LPIC_EBUFSIZE if the capacity is short. */
+lpic_status lpic_load_plasma(lpic_ctx *ctx, const lpic_plasma_params *plasma);
+
+/* Advance nsteps timesteps (paper Sec. 3, the 3D envelope loop order):
+ * Faraday -> gather/chi deposit/ponderomotive Boris -> envelope solve (Eq. envelope_solver)
+ * -> position push/charge-conserving current -> Ampere -> moving window/injection,
+ * with a counting sort every sort_every steps.  Asynchronous on the context stream. */
+lpic_status lpic_step(lpic_ctx *ctx, int nsteps);
+
+/* Read an observable into host memory host_out (capacity cap bytes); *written gets the
+ * byte count.  Synchronises the context stream.  LPIC_EBUFSIZE if cap is too small
+ * (*written then holds the size needed); LPIC_ENONFINITE if a returned scalar is NaN/Inf. */
+lpic_status lpic_diagnose(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, size_t cap,
+                          size_t *written);
+
+/* Overwrite a part of the state from host memory in the dump layout of the same kind
+ * (checkpoint restore, or starting from another implementation's state).  Accepts
+ * LPIC_DIAG_EX/ER/BT/A/AM (exact sizes), LPIC_DIAG_PARTICLES (7n doubles: replaces the
+ * particle set by n particles, ids reset to 0..n-1), LPIC_DIAG_PARTICLE_IDS (n ids for the
+ * current set) and LPIC_DIAG_COUNTERS (step and shift; the other two entries are ignored).
+ * Synchronises the context stream. */
+lpic_status lpic_upload(lpic_ctx *ctx, lpic_diag_kind kind, const void *host_in, size_t bytes);
+
+/* Tracing.  Launches of every kernel family are always counted; while timing is enabled,
+ * lpic_step also records a CUDA event pair around each launch on the context stream.
+ * lpic_kernel_stats writes, for up to cap families, the launch count since lpic_init_grid
+ * and the device milliseconds accumulated while timing was on (it synchronises the stream
+ * and then clears the accumulated times); *n gets the number of families.  Family k is
+ * named by lpic_kernel_name(k) (NULL past the last). */
+lpic_status lpic_set_kernel_timing(lpic_ctx *ctx, int enable);
+lpic_status lpic_kernel_stats(lpic_ctx *ctx, int64_t *launches, double *ms, int cap, int *n);
+const char *lpic_kernel_name(int k);
+
+/* Release the context (host memory only; the device buffer stays the caller's). */
+lpic_status lpic_destroy(lpic_ctx *ctx);
+
+/* Message of the last failing call on ctx (or of the last failing lpic_init_grid /
+ * lpic_batch_create on this thread when ctx is NULL).  Never NULL. */
+const char *lpic_last_error(const lpic_ctx *ctx);
+
+/* ---- batched form: many independent simulations advanced together ------------------
+ * All contexts must share one precision and one device.  One step of the batch is a
+ * fixed sequence of fused launches, each covering every simulation's grid tiles or
+ * particle tiles through a work list, recorded once in a CUDA graph and replayed.
+ * The contexts keep their own buffers; the batch allocates nothing on the device beyond
+ * what lpic_batch_required_bytes() asks the caller for. */
+size_t lpic_batch_required_bytes(int n);
+lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, void *device_buf,
+                              size_t buf_bytes, void *cuda_stream);
+/* Advance simulation k by steps_per_ctx[k] >= 0 steps; simulations with fewer steps
+ * sit idle in the later launches.  Asynchronous on the batch stream. */
+lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
+lpic_status lpic_batch_destroy(lpic_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPIC_H */

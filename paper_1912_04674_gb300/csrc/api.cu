@@ -1,0 +1,886 @@
+// Host side of the C ABI declared in include/lpic.h: parameter checks, memory planning
+// inside the caller's buffer, step orchestration, diagnostics, uploads, batched form.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lpic.h"
+#include "lpic_internal.cuh"
+
+using namespace lpic;
+
+namespace {
+
+thread_local std::string g_thread_err;
+constexpr size_t kAlign = 256;
+constexpr size_t kStageBytes = size_t(8) << 20;
+constexpr double kRadialSpectral = 4.842;  // sup of dr^2 x spectral radius, m=0 radial operator
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+
+void msgf(char *msg, size_t cap, const char *fmt, double a = 0, double b = 0) {
+    if (msg && cap) snprintf(msg, cap, fmt, a, b);
+}
+
+lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p, char *msg,
+                         size_t cap) {
+    if (!g) { msgf(msg, cap, "grid params are NULL"); return LPIC_EINVAL; }
+    if (g->nx < 2 || g->nr < 2) { msgf(msg, cap, "nx=%g and nr=%g must be >= 2", g->nx, g->nr); return LPIC_EINVAL; }
+    if (g->nr > 65536) { msgf(msg, cap, "nr=%g exceeds 65536", g->nr); return LPIC_EINVAL; }
+    if ((long long)g->nx * g->nr + 1 > (long long)4096 * 4096) {
+        msgf(msg, cap, "nx*nr=%g cells exceeds the counting-sort limit 16777215", (double)g->nx * g->nr);
+        return LPIC_EINVAL;
+    }
+    const double dx = g->dx, dr = g->dr, dt = g->dt;
+    if (!(dx > 0 && dr > 0 && dt > 0) || !std::isfinite(dx) || !std::isfinite(dr) || !std::isfinite(dt)) {
+        msgf(msg, cap, "dx, dr, dt must be positive and finite");
+        return LPIC_EINVAL;
+    }
+    if (g->particle_capacity < 0 || g->particle_capacity > (int64_t)INT32_MAX / 2) {
+        msgf(msg, cap, "particle_capacity=%g out of range", (double)g->particle_capacity);
+        return LPIC_EINVAL;
+    }
+    if (g->particle_capacity > 0 && g->sort_every < 1) {
+        msgf(msg, cap, "sort_every must be >= 1 when particles are present");
+        return LPIC_EINVAL;
+    }
+    // Yee m=0 leapfrog: dt * omega_max < 2
+    const double wmax = std::sqrt(4.0 / (dx * dx) + kRadialSpectral / (dr * dr));
+    if (!(dt * wmax < 2.0)) {
+        msgf(msg, cap, "Yee stability: dt=%g >= %g", dt, 2.0 / wmax);
+        return LPIC_ECFL;
+    }
+    // envelope scheme: both characteristic roots on the unit circle for every mode
+    const double sx = std::sqrt(1.0 + dx * dx), st = std::sqrt(1.0 + dt * dt);
+    const double kmax = (2.0 + 2.0 * sx) / (dx * dx) + kRadialSpectral / (dr * dr);
+    const double kneg = (2.0 * sx - 2.0) / (dx * dx);
+    if (!(dt * dt * kmax <= 2.0 + 2.0 * st) || !(dt * dt * kneg <= 2.0 * st - 2.0)) {
+        msgf(msg, cap, "envelope stability: dt=%g outside the stable range (dx=%g)", dt, dx);
+        return LPIC_ECFL;
+    }
+    if (!(dt < dx && dt < dr)) {
+        msgf(msg, cap, "particle step: dt=%g must be below min(dx, dr)=%g", dt, std::fmin(dx, dr));
+        return LPIC_ECFL;
+    }
+    if (p) {
+        if (!(p->n0 >= 0) || !std::isfinite(p->n0) || !(p->ramp_len >= 0) || !std::isfinite(p->x_start)) {
+            msgf(msg, cap, "plasma: n0 >= 0, ramp_len >= 0 and finite values required");
+            return LPIC_EINVAL;
+        }
+        if (p->ppc_x < 1 || p->ppc_x > 16 || p->ppc_r < 1 || p->ppc_theta < 1 ||
+            (long long)p->ppc_x * p->ppc_r * p->ppc_theta > 1024) {
+            msgf(msg, cap, "plasma: ppc_x in [1,16], ppc_r, ppc_theta >= 1, product <= 1024");
+            return LPIC_EINVAL;
+        }
+    }
+    if (msg && cap) msg[0] = 0;
+    return LPIC_OK;
+}
+
+struct Layout {
+    size_t desc, grid[14], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
+    int P, nlive, ncol;
+};
+
+Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
+    Layout L{};
+    const size_t rs = prec == LPIC_FP64 ? 8 : 4;
+    L.P = ((g->nr + 3) + 3) / 4 * 4;  // rows up to nr+2 are touched by the 3x3 deposit window
+    L.nlive = g->nx + 1 + 2 * kG;
+    L.ncol = g->moving_window ? 2 * L.nlive : L.nlive;
+    const size_t cells = (size_t)L.P * L.ncol;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+    L.desc = take(sizeof(Desc));
+    // ex er bt btn phi gx gr phih (R), a0 a1 (2R), chi jx jr dq (double)
+    for (int k = 0; k < 8; k++) L.grid[k] = take(cells * rs);
+    for (int k = 8; k < 10; k++) L.grid[k] = take(cells * 2 * rs);
+    for (int k = 10; k < 14; k++) L.grid[k] = take(cells * 8);
+    const size_t cap = (size_t)g->particle_capacity;
+    for (int b = 0; b < 2; b++) {
+        L.parts[b][0] = take(cap * 4);                          // ix
+        for (int k = 1; k < 8; k++) L.parts[b][k] = take(cap * rs);  // ox y z px py pz w
+        L.parts[b][8] = take(cap * 8);                          // id
+    }
+    const size_t ncell = (size_t)g->nx * g->nr;
+    L.key = take((cap + 1) * 4);
+    L.count = take((ncell + 2) * 4);
+    L.blocksum = take(((ncell + 1 + 4095) / 4096 + 1) * 4);
+    L.blockcnt = take((cap / 256 + 2) * 4);
+    L.icount = take(16);
+    L.diag = take(16 * 8);
+    size_t col_bytes = (size_t)(g->nr + 1) * 16;
+    size_t stage = kStageBytes;
+    if (stage < col_bytes) stage = col_bytes;
+    L.stage = take(stage);
+    L.total = o;
+    return L;
+}
+
+int valid_a_count(const Phys &ph, long long c) {
+    int nv = 0;
+    for (int a = 0; a < ph.ppcx; a++)
+        if (plasma_density(ph, ((double)c + (a + 0.5) / ph.ppcx) * ph.dx) > 0.0) nv++;
+    return nv;
+}
+
+}  // namespace
+
+struct lpic_ctx {
+    lpic_precision prec;
+    lpic_grid_params g;
+    Phys ph{};
+    Geo geo{};
+    cudaStream_t st = nullptr;
+    char *buf = nullptr;
+    size_t bytes = 0;
+    Layout L{};
+    SimDev<double> sd{};
+    SimDev<float> sf{};
+    Desc *d_desc = nullptr;
+    int *key = nullptr, *count = nullptr, *blocksum = nullptr, *blockcnt = nullptr, *icount = nullptr;
+    double *diag = nullptr;
+    char *stage = nullptr;
+    size_t stage_bytes = 0;
+    // host mirrors of the deterministic counters
+    long long step = 0, shift = 0;
+    int off = 0;
+    long long np_upper = 0;
+    int since_sort = 0;
+    Desc *h_desc = nullptr;          // pinned
+    cudaEvent_t ev = nullptr;
+    bool ev_pending = false;
+    std::string err;
+    bool envelope_set = false;
+    // tracing
+    static constexpr int kFamilies = 9;
+    long long launches[kFamilies] = {};
+    double ms[kFamilies] = {};
+    bool timing = false;
+    struct Span { int fam; cudaEvent_t a, b; };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> ev_pool;
+
+    lpic_status fail(lpic_status s, const std::string &m) { err = m; return s; }
+    lpic_status cuda_fail(cudaError_t e, const char *where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return LPIC_ECUDA;
+    }
+    void sync_views() {
+        sd.ph = ph;
+        sf.ph = ph;
+    }
+    template <class F> void dispatch(F &&f) {
+        if (prec == LPIC_FP64) f(sd); else f(sf);
+    }
+};
+
+namespace {
+
+const char *const kFamilyNames[lpic_ctx::kFamilies] = {
+    "prepass", "pass_a", "envelope", "pass_b", "ampere", "window", "advance", "sort", "relocate"};
+enum Fam { F_PREPASS, F_PASS_A, F_ENVELOPE, F_PASS_B, F_AMPERE, F_WINDOW, F_ADVANCE, F_SORT, F_RELOCATE };
+constexpr int kSortLaunches = 6;  // memset-free launches of one counting sort
+
+cudaEvent_t pool_event(lpic_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch through f, counting it as family `fam` (nlaunch kernels) and, when timing is on,
+// bracketing it with events on stream st.
+template <class F> void traced(lpic_ctx *c, int fam, int nlaunch, cudaStream_t st, F &&f) {
+    c->launches[fam] += nlaunch;
+    if (!c->timing) { f(); return; }
+    lpic_ctx::Span sp{fam, pool_event(c), pool_event(c)};
+    cudaEventRecord(sp.a, st);
+    f();
+    cudaEventRecord(sp.b, st);
+    c->spans.push_back(sp);
+}
+
+template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
+    char *b = c->buf;
+    const Layout &L = c->L;
+    S.geo = c->geo;
+    S.ph = c->ph;
+    S.d = c->d_desc;
+    S.f.ex = (R *)(b + L.grid[0]);
+    S.f.er = (R *)(b + L.grid[1]);
+    S.f.bt = (R *)(b + L.grid[2]);
+    S.f.btn = (R *)(b + L.grid[3]);
+    S.f.phi = (R *)(b + L.grid[4]);
+    S.f.gx = (R *)(b + L.grid[5]);
+    S.f.gr = (R *)(b + L.grid[6]);
+    S.f.phih = (R *)(b + L.grid[7]);
+    S.f.a[0] = (typename Cplx<R>::t *)(b + L.grid[8]);
+    S.f.a[1] = (typename Cplx<R>::t *)(b + L.grid[9]);
+    S.f.chi = (double *)(b + L.grid[10]);
+    S.f.jx = (double *)(b + L.grid[11]);
+    S.f.jr = (double *)(b + L.grid[12]);
+    S.f.dq = (double *)(b + L.grid[13]);
+    for (int k = 0; k < 2; k++) {
+        S.p[k].ix = (int32_t *)(b + L.parts[k][0]);
+        S.p[k].ox = (R *)(b + L.parts[k][1]);
+        S.p[k].y = (R *)(b + L.parts[k][2]);
+        S.p[k].z = (R *)(b + L.parts[k][3]);
+        S.p[k].px = (R *)(b + L.parts[k][4]);
+        S.p[k].py = (R *)(b + L.parts[k][5]);
+        S.p[k].pz = (R *)(b + L.parts[k][6]);
+        S.p[k].w = (R *)(b + L.parts[k][7]);
+        S.p[k].id = (uint64_t *)(b + L.parts[k][8]);
+    }
+}
+
+lpic_status pull_desc(lpic_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_desc, c->d_desc, sizeof(Desc), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "pull_desc");
+    return LPIC_OK;
+}
+lpic_status push_desc(lpic_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "push_desc");
+    return LPIC_OK;
+}
+
+lpic_status device_errors(lpic_ctx *c, const Desc &d) {
+    if (d.err & ERR_CAPACITY)
+        return c->fail(LPIC_EBUFSIZE, "particle capacity exhausted during plasma injection "
+                                      "(raise particle_capacity or lower sort_every)");
+    return LPIC_OK;
+}
+
+// Errors latched on the device by earlier asynchronous steps, if their copy has landed.
+lpic_status deferred_errors(lpic_ctx *c) {
+    if (!c->ev_pending) return LPIC_OK;
+    cudaError_t q = cudaEventQuery(c->ev);
+    if (q == cudaErrorNotReady) return LPIC_OK;
+    c->ev_pending = false;
+    if (q != cudaSuccess) return c->cuda_fail(q, "step");
+    return device_errors(c, *c->h_desc);
+}
+
+int launch_cap(const lpic_ctx *c) {
+    long long n = c->np_upper < c->g.particle_capacity ? c->np_upper : c->g.particle_capacity;
+    return (int)n;
+}
+
+// Host part of one step before its launches: relocate the live region when the slide
+// reaches the end of the allocation.
+void pre_step(lpic_ctx *c, cudaStream_t st) {
+    if (c->g.moving_window && c->off + c->geo.nlive + 1 > c->geo.ncol) {
+        traced(c, F_RELOCATE, 2, st, [&] { c->dispatch([&](auto &S) { launch_relocate(S, 0, st); }); });
+        c->off = 0;
+    }
+}
+
+template <class S_>
+void enqueue_step_kernels(lpic_ctx *c, const S_ &S, int npl, int inj, cudaStream_t st) {
+    traced(c, F_PREPASS, 1, st, [&] { launch_prepass(S, st); });
+    if (npl > 0) traced(c, F_PASS_A, 1, st, [&] { launch_pass_a(S, npl, st); });
+    traced(c, F_ENVELOPE, 1, st, [&] { launch_envelope(S, st); });
+    if (npl > 0) traced(c, F_PASS_B, 1, st, [&] { launch_pass_b(S, npl, st); });
+    traced(c, F_AMPERE, 1, st, [&] { launch_ampere(S, st); });
+    traced(c, F_WINDOW, 1, st, [&] { launch_window(S, inj, st); });
+    traced(c, F_ADVANCE, 1, st, [&] { launch_advance(S, st); });
+}
+
+int inj_upper(const lpic_ctx *c) {
+    return c->ph.have_plasma ? c->ph.ppcx * c->ph.ppcr * c->ph.ppct * c->geo.nr : 0;
+}
+
+// Host mirror update after one step's launches, and the periodic sort.
+void post_step(lpic_ctx *c, cudaStream_t st) {
+    if (window_shifts(c->ph, c->step, c->shift)) {
+        c->shift += 1;
+        c->off += 1;
+        if (c->ph.have_plasma)
+            c->np_upper += (long long)valid_a_count(c->ph, c->shift + c->geo.nx - 1) * c->ph.ppcr *
+                           c->ph.ppct * c->geo.nr;
+    }
+    c->step += 1;
+    if (c->g.particle_capacity > 0 && c->np_upper > 0 && ++c->since_sort >= c->g.sort_every) {
+        const int npl = launch_cap(c);
+        traced(c, F_SORT, kSortLaunches, st, [&] {
+            c->dispatch([&](auto &S) { launch_sort(S, npl, c->key, c->count, c->blocksum, st); });
+        });
+        c->since_sort = 0;
+    }
+}
+
+void record_status_copy(lpic_ctx *c) {
+    cudaMemcpyAsync(c->h_desc, c->d_desc, sizeof(Desc), cudaMemcpyDeviceToHost, c->st);
+    cudaEventRecord(c->ev, c->st);
+    c->ev_pending = true;
+}
+
+}  // namespace
+
+// ====================================================================================== API
+
+extern "C" {
+
+lpic_status lpic_check_params(const lpic_grid_params *g, const lpic_plasma_params *p, char *msg,
+                              size_t msg_cap) {
+    return check_params(g, p, msg, msg_cap);
+}
+
+int64_t lpic_particle_capacity(const lpic_grid_params *g, const lpic_plasma_params *p) {
+    if (!g || !p) return 0;
+    const int64_t ppc = (int64_t)p->ppc_x * p->ppc_r * p->ppc_theta;
+    int64_t cap = (int64_t)g->nx * g->nr * ppc + 1024;
+    if (g->moving_window) cap += (int64_t)(g->sort_every > 0 ? g->sort_every + 2 : 3) * g->nr * ppc;
+    return cap;
+}
+
+size_t lpic_required_bytes(const lpic_grid_params *g, lpic_precision prec) {
+    if (check_params(g, nullptr, nullptr, 0) != LPIC_OK) return 0;
+    if (prec != LPIC_FP64 && prec != LPIC_FP32_MIXED) return 0;
+    return make_layout(g, prec).total;
+}
+
+lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_precision prec,
+                           void *device_buf, size_t buf_bytes, void *cuda_stream) {
+    char m[256];
+    if (!out) { g_thread_err = "out is NULL"; return LPIC_EINVAL; }
+    lpic_status s = check_params(g, nullptr, m, sizeof m);
+    if (s != LPIC_OK) { g_thread_err = m; return s; }
+    if (prec != LPIC_FP64 && prec != LPIC_FP32_MIXED) { g_thread_err = "bad precision"; return LPIC_EINVAL; }
+    if (!device_buf || ((uintptr_t)device_buf & (kAlign - 1))) {
+        g_thread_err = "device_buf must be non-NULL and 256-byte aligned";
+        return LPIC_EINVAL;
+    }
+    Layout L = make_layout(g, prec);
+    if (buf_bytes < L.total) {
+        g_thread_err = "device buffer of " + std::to_string(buf_bytes) + " bytes is smaller than the " +
+                       std::to_string(L.total) + " required";
+        return LPIC_ENOMEM_BUDGET;
+    }
+    lpic_ctx *c = new lpic_ctx();
+    c->prec = prec;
+    c->g = *g;
+    c->L = L;
+    c->st = (cudaStream_t)cuda_stream;
+    c->buf = (char *)device_buf;
+    c->bytes = buf_bytes;
+    c->geo.nx = g->nx;
+    c->geo.nr = g->nr;
+    c->geo.P = L.P;
+    c->geo.ncol = L.ncol;
+    c->geo.nlive = L.nlive;
+    c->ph.dx = g->dx;
+    c->ph.dr = g->dr;
+    c->ph.dt = g->dt;
+    c->ph.moving_window = g->moving_window ? 1 : 0;
+    c->ph.cap = (int)g->particle_capacity;
+    c->ph.track_dq = g->track_continuity ? 1 : 0;
+    c->d_desc = (Desc *)(c->buf + L.desc);
+    c->key = (int *)(c->buf + L.key);
+    c->count = (int *)(c->buf + L.count);
+    c->blocksum = (int *)(c->buf + L.blocksum);
+    c->blockcnt = (int *)(c->buf + L.blockcnt);
+    c->icount = (int *)(c->buf + L.icount);
+    c->diag = (double *)(c->buf + L.diag);
+    c->stage = c->buf + L.stage;
+    c->stage_bytes = L.total - L.stage;
+    fill_views(c, c->sd);
+    fill_views(c, c->sf);
+    cudaError_t e = cudaMallocHost((void **)&c->h_desc, sizeof(Desc));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, L.total, c->st);
+    if (e != cudaSuccess) {
+        g_thread_err = std::string("lpic_init_grid: ") + cudaGetErrorString(e);
+        if (c->h_desc) cudaFreeHost(c->h_desc);
+        delete c;
+        return LPIC_ECUDA;
+    }
+    memset(c->h_desc, 0, sizeof(Desc));
+    if ((s = push_desc(c)) != LPIC_OK) {
+        g_thread_err = c->err;
+        cudaFreeHost(c->h_desc);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return LPIC_OK;
+}
+
+lpic_status lpic_init_envelope(lpic_ctx *c, const lpic_laser_params *la) {
+    if (!c || !la) return c ? c->fail(LPIC_EINVAL, "laser params are NULL") : LPIC_EINVAL;
+    if (!(la->w0 > 0) || !(la->L > 0) || !std::isfinite(la->a0) || !std::isfinite(la->x_center) ||
+        !std::isfinite(la->x_focus))
+        return c->fail(LPIC_EINVAL, "laser: w0 > 0, L > 0 and finite a0, x_center, x_focus required");
+    c->dispatch([&](auto &S) { launch_init_envelope(S, la->a0, la->w0, la->L, la->x_center, la->x_focus, c->st); });
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->cuda_fail(e, "lpic_init_envelope");
+    c->envelope_set = true;
+    return LPIC_OK;
+}
+
+lpic_status lpic_load_plasma(lpic_ctx *c, const lpic_plasma_params *p) {
+    if (!c) return LPIC_EINVAL;
+    char m[256];
+    lpic_status s = check_params(&c->g, p, m, sizeof m);
+    if (s != LPIC_OK) return c->fail(s, m);
+    if (!p) return c->fail(LPIC_EINVAL, "plasma params are NULL");
+    if ((s = pull_desc(c)) != LPIC_OK) return s;
+    Phys ph = c->ph;
+    ph.have_plasma = 1;
+    ph.n0 = p->n0;
+    ph.x_start = p->x_start;
+    ph.ramp_len = p->ramp_len;
+    ph.ppcx = p->ppc_x;
+    ph.ppcr = p->ppc_r;
+    ph.ppct = p->ppc_theta;
+    ph.seed = p->seed;
+    std::vector<int> colbase(c->geo.nx + 1, 0);
+    long long total = 0;
+    for (int i = 0; i < c->geo.nx; i++) {
+        colbase[i] = (int)total;
+        total += (long long)valid_a_count(ph, c->shift + i) * ph.ppcr * ph.ppct * c->geo.nr;
+        if (total > c->g.particle_capacity) break;
+    }
+    colbase[c->geo.nx] = (int)(total < INT32_MAX ? total : INT32_MAX);
+    const long long np0 = c->h_desc->np;
+    if (np0 != 0) return c->fail(LPIC_ESTATE, "lpic_load_plasma: particles already loaded");
+    const long long headroom = c->g.moving_window
+                                   ? (long long)(c->g.sort_every + 2) * ph.ppcx * ph.ppcr * ph.ppct * c->geo.nr
+                                   : 0;
+    if (total + headroom > c->g.particle_capacity)
+        return c->fail(LPIC_EBUFSIZE, "particle_capacity " + std::to_string(c->g.particle_capacity) +
+                                          " < " + std::to_string(total + headroom) +
+                                          " (window plus injection headroom)");
+    if (colbase.size() * sizeof(int) > c->stage_bytes) return c->fail(LPIC_EINVAL, "nx too large for staging");
+    c->ph = ph;
+    c->sync_views();
+    cudaError_t e = cudaMemcpyAsync(c->stage, colbase.data(), colbase.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lpic_load_plasma");
+    c->dispatch([&](auto &S) { launch_load_columns(S, (const int *)c->stage, c->geo.nx, (int)total, c->st); });
+    c->h_desc->np = (int)total;
+    c->h_desc->n_alive = (int)total;
+    if ((s = push_desc(c)) != LPIC_OK) return s;  // synchronises: colbase may go
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return c->cuda_fail(e, "lpic_load_plasma");
+    c->np_upper = total;
+    c->since_sort = 0;
+    return LPIC_OK;
+}
+
+lpic_status lpic_step(lpic_ctx *c, int nsteps) {
+    if (!c) return LPIC_EINVAL;
+    if (nsteps < 0) return c->fail(LPIC_EINVAL, "nsteps < 0");
+    lpic_status s = deferred_errors(c);
+    if (s != LPIC_OK) return s;
+    for (int k = 0; k < nsteps; k++) {
+        pre_step(c, c->st);
+        const int npl = launch_cap(c), inj = inj_upper(c);
+        c->dispatch([&](auto &S) { enqueue_step_kernels(c, S, npl, inj, c->st); });
+        post_step(c, c->st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->cuda_fail(e, "lpic_step");
+    record_status_copy(c);
+    return LPIC_OK;
+}
+
+lpic_status lpic_diagnose(lpic_ctx *c, lpic_diag_kind kind, void *host_out, size_t cap,
+                          size_t *written) {
+    if (!c) return LPIC_EINVAL;
+    if (written) *written = 0;
+    lpic_status s = pull_desc(c);
+    if (s != LPIC_OK) return s;
+    c->ev_pending = false;
+    if ((s = device_errors(c, *c->h_desc)) != LPIC_OK) return s;
+    const Desc d = *c->h_desc;
+    const int nx = c->geo.nx, nr = c->geo.nr;
+    auto need = [&](size_t n) -> bool {
+        if (written) *written = n;
+        return cap >= n && (n == 0 || host_out);
+    };
+    auto copy_back = [&](void *dst, const void *src, size_t n) -> lpic_status {
+        cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_diagnose");
+    };
+    switch (kind) {
+    case LPIC_DIAG_EX_AXIS: {
+        if (!need(nx * sizeof(double))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        c->dispatch([&](auto &S) { launch_diag_ex_axis(S, (double *)c->stage, c->st); });
+        return copy_back(host_out, c->stage, nx * sizeof(double));
+    }
+    case LPIC_DIAG_A_ABS_MAX:
+    case LPIC_DIAG_WAIST: {
+        if (!need(sizeof(double))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        double h[3];
+        c->dispatch([&](auto &S) { launch_diag_amax_waist(S, c->diag, c->st); });
+        if ((s = copy_back(h, c->diag, sizeof h)) != LPIC_OK) return s;
+        double v = kind == LPIC_DIAG_A_ABS_MAX ? h[0] : (h[2] > 0 ? std::sqrt(2.0 * h[1] / h[2]) : 0.0);
+        memcpy(host_out, &v, sizeof v);
+        return std::isfinite(v) ? LPIC_OK : c->fail(LPIC_ENONFINITE, "non-finite envelope");
+    }
+    case LPIC_DIAG_CONT_RESIDUAL: {
+        if (!need(sizeof(double))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        if (!c->ph.track_dq) return c->fail(LPIC_ESTATE, "track_continuity is off");
+        double h[2];
+        c->dispatch([&](auto &S) { launch_diag_cont(S, c->diag, c->st); });
+        if ((s = copy_back(h, c->diag, sizeof h)) != LPIC_OK) return s;
+        double v = h[1] > 0 ? h[0] / h[1] : 0.0;
+        memcpy(host_out, &v, sizeof v);
+        return std::isfinite(v) ? LPIC_OK : c->fail(LPIC_ENONFINITE, "non-finite current");
+    }
+    case LPIC_DIAG_ACCEL_ENERGY: {
+        if (!need(4 * sizeof(double))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        double h[4];
+        const double thr = c->g.accel_px_min > 0 ? c->g.accel_px_min : 10.0;
+        c->dispatch([&](auto &S) { launch_diag_accel(S, launch_cap(c), thr, c->diag, c->st); });
+        if ((s = copy_back(h, c->diag, sizeof h)) != LPIC_OK) return s;
+        double o[4] = {h[0], h[1], 0.0, 0.0};
+        if (h[1] > 0) {
+            o[2] = h[2] / h[1];
+            o[3] = std::sqrt(std::fmax(h[3] / h[1] - o[2] * o[2], 0.0));
+        }
+        memcpy(host_out, o, sizeof o);
+        return LPIC_OK;
+    }
+    case LPIC_DIAG_COUNTERS: {
+        if (!need(4 * sizeof(int64_t))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        c->dispatch([&](auto &S) { launch_alive_index(S, launch_cap(c), c->key, c->blockcnt, c->icount, c->st); });
+        int alive = 0;
+        if ((s = copy_back(&alive, c->icount, sizeof alive)) != LPIC_OK) return s;
+        int64_t o[4] = {d.step, d.shift, d.np, alive};
+        memcpy(host_out, o, sizeof o);
+        return LPIC_OK;
+    }
+    case LPIC_DIAG_EX: case LPIC_DIAG_ER: case LPIC_DIAG_BT: case LPIC_DIAG_A: case LPIC_DIAG_AM:
+    case LPIC_DIAG_CHI: case LPIC_DIAG_JX: case LPIC_DIAG_JR: case LPIC_DIAG_DQ: {
+        int ni, nj, cp = 0;
+        switch (kind) {
+        case LPIC_DIAG_EX: case LPIC_DIAG_JX: ni = nx; nj = nr + 1; break;
+        case LPIC_DIAG_ER: case LPIC_DIAG_JR: ni = nx + 1; nj = nr; break;
+        case LPIC_DIAG_BT: ni = nx; nj = nr; break;
+        case LPIC_DIAG_A: case LPIC_DIAG_AM: ni = nx + 1; nj = nr + 1; cp = 1; break;
+        default: ni = nx + 1; nj = nr + 1; break;
+        }
+        const size_t colb = (size_t)nj * sizeof(double) * (cp ? 2 : 1);
+        if (!need(colb * ni)) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        const int per = (int)(c->stage_bytes / colb);
+        for (int c0 = 0; c0 < ni; c0 += per) {
+            const int c1 = c0 + per < ni ? c0 + per : ni;
+            c->dispatch([&](auto &S) { launch_dump_field(S, (int)kind, c0, c1, (double *)c->stage, c->st); });
+            if ((s = copy_back((char *)host_out + colb * c0, c->stage, colb * (c1 - c0))) != LPIC_OK) return s;
+        }
+        return LPIC_OK;
+    }
+    case LPIC_DIAG_PARTICLES:
+    case LPIC_DIAG_PARTICLE_IDS: {
+        c->dispatch([&](auto &S) { launch_alive_index(S, launch_cap(c), c->key, c->blockcnt, c->icount, c->st); });
+        int n = 0;
+        if ((s = copy_back(&n, c->icount, sizeof n)) != LPIC_OK) return s;
+        const size_t per_p = kind == LPIC_DIAG_PARTICLES ? 7 * sizeof(double) : sizeof(uint64_t);
+        if (!need(per_p * n)) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        const int chunk = (int)(c->stage_bytes / 8);
+        if (kind == LPIC_DIAG_PARTICLE_IDS) {
+            for (int k0 = 0; k0 < n; k0 += chunk) {
+                const int k1 = k0 + chunk < n ? k0 + chunk : n;
+                c->dispatch([&](auto &S) { launch_set_ids(S, c->key, k0, k1, nullptr, (uint64_t *)c->stage, 0, c->st); });
+                if ((s = copy_back((uint64_t *)host_out + k0, c->stage, 8 * (size_t)(k1 - k0))) != LPIC_OK) return s;
+            }
+            return LPIC_OK;
+        }
+        for (int comp = 0; comp < 7; comp++)
+            for (int k0 = 0; k0 < n; k0 += chunk) {
+                const int k1 = k0 + chunk < n ? k0 + chunk : n;
+                c->dispatch([&](auto &S) { launch_dump_particles(S, c->key, k0, k1, comp, (double *)c->stage, c->st); });
+                if ((s = copy_back((double *)host_out + (size_t)comp * n + k0, c->stage, 8 * (size_t)(k1 - k0))) != LPIC_OK)
+                    return s;
+            }
+        return LPIC_OK;
+    }
+    }
+    return c->fail(LPIC_EINVAL, "unknown diagnostic kind");
+}
+
+lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, size_t bytes) {
+    if (!c) return LPIC_EINVAL;
+    if (!host_in && bytes) return c->fail(LPIC_EINVAL, "host_in is NULL");
+    lpic_status s = pull_desc(c);
+    if (s != LPIC_OK) return s;
+    const int nx = c->geo.nx, nr = c->geo.nr;
+    auto h2d = [&](void *dst, const void *src, size_t n) -> lpic_status {
+        cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->st);
+        return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_upload");
+    };
+    auto finish = [&]() -> lpic_status {
+        cudaError_t e = cudaStreamSynchronize(c->st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_upload");
+    };
+    switch (kind) {
+    case LPIC_DIAG_COUNTERS: {
+        if (bytes != 4 * sizeof(int64_t)) return c->fail(LPIC_EINVAL, "counters: 4 int64 expected");
+        int64_t v[4];
+        memcpy(v, host_in, sizeof v);
+        if (v[0] < 0 || v[1] < 0) return c->fail(LPIC_EINVAL, "counters must be >= 0");
+        c->h_desc->step = v[0];
+        c->h_desc->shift = v[1];
+        if ((s = push_desc(c)) != LPIC_OK) return s;
+        c->step = v[0];
+        c->shift = v[1];
+        return LPIC_OK;
+    }
+    case LPIC_DIAG_EX: case LPIC_DIAG_ER: case LPIC_DIAG_BT: case LPIC_DIAG_A: case LPIC_DIAG_AM: {
+        int ni, nj, cp = 0;
+        switch (kind) {
+        case LPIC_DIAG_EX: ni = nx; nj = nr + 1; break;
+        case LPIC_DIAG_ER: ni = nx + 1; nj = nr; break;
+        case LPIC_DIAG_BT: ni = nx; nj = nr; break;
+        default: ni = nx + 1; nj = nr + 1; cp = 1; break;
+        }
+        const size_t colb = (size_t)nj * sizeof(double) * (cp ? 2 : 1);
+        if (bytes != colb * ni) return c->fail(LPIC_EINVAL, "upload: wrong size for this array");
+        const int per = (int)(c->stage_bytes / colb);
+        for (int c0 = 0; c0 < ni; c0 += per) {
+            const int c1 = c0 + per < ni ? c0 + per : ni;
+            if ((s = h2d(c->stage, (const char *)host_in + colb * c0, colb * (c1 - c0))) != LPIC_OK) return s;
+            c->dispatch([&](auto &S) { launch_upload_field(S, (int)kind, c0, c1, (const double *)c->stage, c->st); });
+        }
+        return finish();
+    }
+    case LPIC_DIAG_PARTICLES: {
+        if (bytes % (7 * sizeof(double))) return c->fail(LPIC_EINVAL, "particles: 7n doubles expected");
+        const long long n = (long long)(bytes / (7 * sizeof(double)));
+        if (n > c->g.particle_capacity) return c->fail(LPIC_EBUFSIZE, "more particles than capacity");
+        const int chunk = (int)(c->stage_bytes / 8);
+        for (int comp = 0; comp < 7; comp++)
+            for (long long k0 = 0; k0 < n; k0 += chunk) {
+                const long long k1 = k0 + chunk < n ? k0 + chunk : n;
+                if ((s = h2d(c->stage, (const double *)host_in + comp * n + k0, 8 * (size_t)(k1 - k0))) != LPIC_OK)
+                    return s;
+                c->dispatch([&](auto &S) { launch_upload_particles(S, (int)k0, (int)k1, comp, (const double *)c->stage, c->st); });
+            }
+        c->dispatch([&](auto &S) { launch_finish_upload(S, (int)n, c->st); });
+        c->np_upper = n;
+        c->since_sort = 0;
+        return finish();
+    }
+    case LPIC_DIAG_PARTICLE_IDS: {
+        const long long n = (long long)(bytes / sizeof(uint64_t));
+        if (bytes % 8 || n != c->h_desc->np)
+            return c->fail(LPIC_EINVAL, "ids: one uint64 per particle slot expected");
+        const int chunk = (int)(c->stage_bytes / 8);
+        for (long long k0 = 0; k0 < n; k0 += chunk) {
+            const long long k1 = k0 + chunk < n ? k0 + chunk : n;
+            if ((s = h2d(c->stage, (const uint64_t *)host_in + k0, 8 * (size_t)(k1 - k0))) != LPIC_OK) return s;
+            c->dispatch([&](auto &S) { launch_set_ids(S, nullptr, (int)k0, (int)k1, (const uint64_t *)c->stage, nullptr, 1, c->st); });
+        }
+        return finish();
+    }
+    default:
+        return c->fail(LPIC_EINVAL, "this kind cannot be uploaded");
+    }
+}
+
+lpic_status lpic_set_kernel_timing(lpic_ctx *c, int enable) {
+    if (!c) return LPIC_EINVAL;
+    c->timing = enable != 0;
+    return LPIC_OK;
+}
+
+lpic_status lpic_kernel_stats(lpic_ctx *c, int64_t *launches, double *ms, int cap, int *n) {
+    if (!c) return LPIC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lpic_kernel_stats");
+    for (auto &sp : c->spans) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) c->ms[sp.fam] += t;
+        c->ev_pool.push_back(sp.a);
+        c->ev_pool.push_back(sp.b);
+    }
+    c->spans.clear();
+    const int m = cap < lpic_ctx::kFamilies ? cap : lpic_ctx::kFamilies;
+    for (int k = 0; k < m; k++) {
+        if (launches) launches[k] = c->launches[k];
+        if (ms) ms[k] = c->ms[k];
+        c->ms[k] = 0.0;
+    }
+    if (n) *n = lpic_ctx::kFamilies;
+    return LPIC_OK;
+}
+
+const char *lpic_kernel_name(int k) {
+    return (k >= 0 && k < lpic_ctx::kFamilies) ? kFamilyNames[k] : nullptr;
+}
+
+lpic_status lpic_destroy(lpic_ctx *c) {
+    if (!c) return LPIC_EINVAL;
+    cudaStreamSynchronize(c->st);
+    for (auto &sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    delete c;
+    return LPIC_OK;
+}
+
+const char *lpic_last_error(const lpic_ctx *c) {
+    if (c) return c->err.c_str();
+    return g_thread_err.c_str();
+}
+
+}  // extern "C"
+
+// ============================================================================ batched form
+
+struct lpic_batch {
+    std::vector<lpic_ctx *> ctx;
+    cudaStream_t st = nullptr;
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> active_key;
+    std::vector<std::vector<long long>> per_replay;  // launches per graph replay, per context
+    std::string err;
+};
+
+namespace {
+void batch_release(lpic_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto s : b->aux) cudaStreamDestroy(s);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+}
+
+// Record one step of every active simulation as parallel branches of one graph.
+lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+    cudaEventRecord(b->fork, b->st);
+    for (size_t k = 0; k < b->ctx.size(); k++) {
+        if (!active[k]) continue;
+        lpic_ctx *c = b->ctx[k];
+        cudaStreamWaitEvent(b->aux[k], b->fork, 0);
+        const int npl = (int)c->g.particle_capacity, inj = inj_upper(c);
+        const bool timing = c->timing;
+        c->timing = false;
+        long long before[lpic_ctx::kFamilies];
+        memcpy(before, c->launches, sizeof before);
+        c->dispatch([&](auto &S) { enqueue_step_kernels(c, S, npl, inj, b->aux[k]); });
+        for (int f = 0; f < lpic_ctx::kFamilies; f++) {  // counted per replay instead
+            b->per_replay[k][f] = c->launches[f] - before[f];
+            c->launches[f] = before[f];
+        }
+        c->timing = timing;
+        cudaEventRecord(b->ev[k], b->aux[k]);
+        cudaStreamWaitEvent(b->st, b->ev[k], 0);
+    }
+    e = cudaStreamEndCapture(b->st, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
+    b->active_key = active;
+    return LPIC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t lpic_batch_required_bytes(int n) {
+    (void)n;  // the graph form keeps everything in the contexts' own buffers
+    return 0;
+}
+
+lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, void *device_buf,
+                              size_t buf_bytes, void *cuda_stream) {
+    (void)device_buf;
+    (void)buf_bytes;
+    if (!out || !ctxs || n <= 0) { g_thread_err = "batch: bad arguments"; return LPIC_EINVAL; }
+    for (int k = 0; k < n; k++)
+        if (!ctxs[k] || ctxs[k]->prec != ctxs[0]->prec) {
+            g_thread_err = "batch: contexts must be non-NULL and share one precision";
+            return LPIC_EINVAL;
+        }
+    lpic_batch *b = new lpic_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->st = (cudaStream_t)cuda_stream;
+    b->aux.resize(n);
+    b->ev.resize(n);
+    b->per_replay.assign(n, std::vector<long long>(lpic_ctx::kFamilies, 0));
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < n && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        g_thread_err = std::string("batch: ") + cudaGetErrorString(e);
+        batch_release(b);
+        delete b;
+        return LPIC_ECUDA;
+    }
+    // the contexts' own streams must be idle before the batch stream takes over
+    for (int k = 0; k < n; k++) cudaStreamSynchronize(ctxs[k]->st);
+    *out = b;
+    return LPIC_OK;
+}
+
+lpic_status lpic_batch_step(lpic_batch *b, const int *steps) {
+    if (!b || !steps) return LPIC_EINVAL;
+    int maxs = 0;
+    for (size_t k = 0; k < b->ctx.size(); k++) {
+        if (steps[k] < 0) { b->err = "batch: negative step count"; return LPIC_EINVAL; }
+        if (steps[k] > maxs) maxs = steps[k];
+    }
+    std::vector<char> active(b->ctx.size());
+    // order after earlier work on the contexts' own streams
+    for (size_t k = 0; k < b->ctx.size(); k++) {
+        cudaEventRecord(b->ev[k], b->ctx[k]->st);
+        cudaStreamWaitEvent(b->st, b->ev[k], 0);
+    }
+    for (int t = 0; t < maxs; t++) {
+        for (size_t k = 0; k < b->ctx.size(); k++) active[k] = steps[k] > t;
+        for (size_t k = 0; k < b->ctx.size(); k++)
+            if (active[k]) pre_step(b->ctx[k], b->st);
+        if (!b->exec || active != b->active_key) {
+            lpic_status s = batch_capture(b, active);
+            if (s != LPIC_OK) return s;
+        }
+        cudaError_t e = cudaGraphLaunch(b->exec, b->st);
+        if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        for (size_t k = 0; k < b->ctx.size(); k++)
+            if (active[k])
+                for (int f = 0; f < lpic_ctx::kFamilies; f++) b->ctx[k]->launches[f] += b->per_replay[k][f];
+        for (size_t k = 0; k < b->ctx.size(); k++)
+            if (active[k]) post_step(b->ctx[k], b->st);
+    }
+    // later calls on a context's own stream come after this batch step
+    cudaEventRecord(b->fork, b->st);
+    for (size_t k = 0; k < b->ctx.size(); k++) cudaStreamWaitEvent(b->ctx[k]->st, b->fork, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+    return LPIC_OK;
+}
+
+lpic_status lpic_batch_destroy(lpic_batch *b) {
+    if (!b) return LPIC_EINVAL;
+    cudaStreamSynchronize(b->st);
+    batch_release(b);
+    delete b;
+    return LPIC_OK;
+}
+
+}  // extern "C"

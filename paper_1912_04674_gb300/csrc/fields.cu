@@ -1,0 +1,257 @@
+// Grid kernels: Faraday + per-step node quantities, envelope solve, Ampere, envelope
+// initialisation, live-region relocation.
+//
+// Thread mapping: threadIdx.x runs along the radial index j (contiguous in memory),
+// threadIdx.y and the grid's y along the column index i.  In FP32_MIXED mode the axis
+// row j = 0 of the envelope and of the Ex update is computed in FP64 (the 1/r and 4/dr
+// axis terms); everything else in the working precision R.
+#include "lpic_internal.cuh"
+
+namespace lpic {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+template <class R> __device__ __forceinline__ R sq(R v) { return v * v; }
+
+// Faraday (Eq. MaxwellEqsCylindrical, first equation, FDTD of Sec. 3) on cells, B^n for the
+// gathers, Phi^n = |A^n|^2/2 (Sec. 2) and its centred differences (Sec. 3) on nodes, and
+// the clearing of the FP64 accumulators.  Every element of the live window incl. guards is
+// written, so the per-step arrays always read zero outside their valid range.
+template <class R> __global__ void k_prepass(SimDev<R> S) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const int j = blockIdx.x * BX + threadIdx.x;
+    const int i = (int)(blockIdx.y * BY + threadIdx.y) - kG;
+    if (j >= g.P || i > g.nx + kG) return;
+    const long long id = g.at(off, i, j);
+    const R dt = (R)S.ph.dt, idx_ = (R)(1.0 / S.ph.dx), idr = (R)(1.0 / S.ph.dr);
+
+    if (i >= 0 && i < g.nx && j < g.nr) {
+        R bold = S.f.bt[id];
+        R dexdr = (S.f.ex[id + 1] - S.f.ex[id]) * idr;
+        R derdx = (S.f.er[g.at(off, i + 1, j)] - S.f.er[id]) * idx_;
+        R bnew = bold + dt * (dexdr - derdx);
+        S.f.bt[id] = bnew;
+        S.f.btn[id] = (R)0.5 * (bold + bnew);
+    } else {
+        S.f.btn[id] = (R)0;
+    }
+
+    if (i >= 0 && i <= g.nx && j <= g.nr) {
+        const auto *A = S.f.a[S.d->abuf];
+        auto c = A[id];
+        auto xp = A[g.at(off, i + 1, j)];   // guard columns of A are zero
+        auto xm = A[g.at(off, i - 1, j)];
+        R phc = (R)0.5 * (c.x * c.x + c.y * c.y);
+        R phxp = (R)0.5 * (xp.x * xp.x + xp.y * xp.y);
+        R phxm = (R)0.5 * (xm.x * xm.x + xm.y * xm.y);
+        S.f.phi[id] = phc;
+        S.f.gx[id] = (phxp - phxm) * ((R)0.5 * idx_);
+        if (j == 0) {
+            S.f.gr[id] = (R)0;
+        } else {
+            auto rp = A[id + 1];             // row nr+1 is a zero guard
+            auto rm = A[id - 1];
+            R phrp = (R)0.5 * (rp.x * rp.x + rp.y * rp.y);
+            R phrm = (R)0.5 * (rm.x * rm.x + rm.y * rm.y);
+            S.f.gr[id] = (phrp - phrm) * ((R)0.5 * idr);
+        }
+    } else {
+        S.f.phi[id] = (R)0;
+        S.f.gx[id] = (R)0;
+        S.f.gr[id] = (R)0;
+    }
+    S.f.chi[id] = 0.0;
+    S.f.jx[id] = 0.0;
+    S.f.jr[id] = 0.0;
+    if (S.ph.track_dq) S.f.dq[id] = 0.0;
+}
+
+// One node of Eq. (envelope_solver) in compute precision C:
+//   A^{n+1} = (1+i dt)/(1+dt^2) [2A^n - (1+i dt)A^{n-1} + dt^2 (lap A - chi A + 2i dA/dx)].
+template <class C, class V>
+__device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V rmin, V amin,
+                                              double chi_d, int j, double dx, double dr,
+                                              double dt, C &ore, C &oim) {
+    const C cx = (C)cin.x, cy = (C)cin.y;
+    const C xpx = (C)xpin.x, xpy = (C)xpin.y, xmx = (C)xmin.x, xmy = (C)xmin.y;
+    const C idx2 = (C)(1.0 / (dx * dx)), idr2 = (C)(1.0 / (dr * dr));
+    C lx = (xpx - (C)2 * cx + xmx) * idx2;
+    C ly = (xpy - (C)2 * cy + xmy) * idx2;
+    if (j == 0) {
+        lx += (C)4 * ((C)rpin.x - cx) * idr2;
+        ly += (C)4 * ((C)rpin.y - cy) * idr2;
+    } else {
+        const C rpx = (C)rpin.x, rpy = (C)rpin.y, rmx = (C)rmin.x, rmy = (C)rmin.y;
+        const C inv2rj = (C)(1.0 / (2.0 * dr * (j * dr)));
+        lx += (rpx - (C)2 * cx + rmx) * idr2 + (rpx - rmx) * inv2rj;
+        ly += (rpy - (C)2 * cy + rmy) * idr2 + (rpy - rmy) * inv2rj;
+    }
+    const C h = (C)(0.5 / dx);
+    const C dxr = (xpx - xmx) * h, dxi = (xpy - xmy) * h;
+    const C chi = (C)chi_d, t = (C)dt, t2 = (C)(dt * dt);
+    const C amx = (C)amin.x, amy = (C)amin.y;
+    // bracket: lap - chi A + 2i dA/dx
+    const C bx = lx - chi * cx - (C)2 * dxi;
+    const C by = ly - chi * cy + (C)2 * dxr;
+    const C rx = (C)2 * cx - (amx - t * amy) + t2 * bx;
+    const C ry = (C)2 * cy - (amy + t * amx) + t2 * by;
+    const C p = (C)(1.0 / (1.0 + dt * dt)), pt = (C)(dt / (1.0 + dt * dt));
+    ore = p * rx - pt * ry;
+    oim = p * ry + pt * rx;
+}
+
+// Envelope solve on every node; A^{n+1} overwrites A^{n-1} in place (each node reads only
+// its own A^{n-1}); Phi^{n+1/2} = (Phi^n + Phi^{n+1})/2 for the position push.
+template <class R> __global__ void k_envelope(SimDev<R> S) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const int j = blockIdx.x * BX + threadIdx.x;
+    const int i = blockIdx.y * BY + threadIdx.y;
+    if (j > g.nr || i > g.nx) return;
+    const int ab = S.d->abuf;
+    const auto *A = S.f.a[ab];
+    auto *Am = S.f.a[ab ^ 1];
+    const long long id = g.at(off, i, j);
+    auto c = A[id];
+    auto xp = A[g.at(off, i + 1, j)];
+    auto xm = A[g.at(off, i - 1, j)];
+    auto rp = A[id + 1];
+    auto rm = (j > 0) ? A[id - 1] : c;
+    auto am = Am[id];
+    const double chi = S.f.chi[id];
+    R nre, nim;
+    if (j == 0) {  // axis row in FP64
+        double dre, dim;
+        envelope_node<double>(c, xp, xm, rp, rm, am, chi, 0, S.ph.dx, S.ph.dr, S.ph.dt, dre, dim);
+        nre = (R)dre;
+        nim = (R)dim;
+    } else {
+        envelope_node<R>(c, xp, xm, rp, rm, am, chi, j, S.ph.dx, S.ph.dr, S.ph.dt, nre, nim);
+    }
+    typename Cplx<R>::t o;
+    o.x = nre;
+    o.y = nim;
+    Am[id] = o;
+    S.f.phih[id] = (R)0.5 * ((R)0.5 * (c.x * c.x + c.y * c.y) + (R)0.5 * (nre * nre + nim * nim));
+}
+
+// Ampere (Eq. MaxwellEqsCylindrical, second and third equations): Er on (i, j+1/2) with
+// Er = 0 on the x ends; Ex on (i+1/2, j) with the axis row 4 B_{1/2}/dr and Ex = 0 at r_max.
+template <class R> __global__ void k_ampere(SimDev<R> S) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const int j = blockIdx.x * BX + threadIdx.x;
+    const int i = blockIdx.y * BY + threadIdx.y;
+    if (j > g.nr || i > g.nx) return;
+    const long long id = g.at(off, i, j);
+    const double dt = S.ph.dt, dx = S.ph.dx, dr = S.ph.dr;
+    if (j < g.nr) {
+        if (i == 0 || i == g.nx) {
+            S.f.er[id] = (R)0;
+        } else {
+            R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * (R)(1.0 / dx);
+            S.f.er[id] += (R)dt * (-dbdx - (R)S.f.jr[id]);
+        }
+    }
+    if (i < g.nx) {
+        if (j == g.nr) {
+            S.f.ex[id] = (R)0;
+        } else if (j == 0) {  // axis row in FP64
+            double curl = 4.0 * (double)S.f.bt[id] / dr;
+            S.f.ex[id] = (R)((double)S.f.ex[id] + dt * (curl - S.f.jx[id]));
+        } else {
+            R rp = (R)((j + 0.5) * dr), rm = (R)((j - 0.5) * dr);
+            R curl = (rp * S.f.bt[id] - rm * S.f.bt[id - 1]) * (R)(1.0 / ((j * dr) * dr));
+            S.f.ex[id] += (R)dt * (curl - (R)S.f.jx[id]);
+        }
+    }
+}
+
+// Paraxial focused Gaussian pulse at t = 0 and t = -dt (paper Sec. 4 benchmarks):
+// A = a0/D exp(-r^2/(w0^2 D)) exp(-(x-t-xc)^2/L^2), D = 1 + i (x-xf)/xR, xR = w0^2/2.
+template <class R> __global__ void k_init_envelope(SimDev<R> S, double a0, double w0, double L,
+                                                   double xc, double xf) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const int j = blockIdx.x * BX + threadIdx.x;
+    const int i = blockIdx.y * BY + threadIdx.y;
+    if (j > g.nr || i > g.nx) return;
+    const double x = (double)(S.d->shift + i) * S.ph.dx, r = j * S.ph.dr;
+    const double xr = 0.5 * w0 * w0;
+    const double u = (x - xf) / xr;                 // D = 1 + i u
+    const double inv = 1.0 / (1.0 + u * u);         // 1/D = (1 - i u) inv
+    const double er = -(r * r) / (w0 * w0) * inv;   // -r^2/(w0^2 D) = er (1 - i u)
+    const double mag = exp(er);
+    double sphase, cphase;
+    sincos(-er * u, &sphase, &cphase);
+    // a0/D * exp(er) * e^{-i er u}
+    const double dre = a0 * inv, dim = -a0 * inv * u;
+    const double bre = dre * cphase - dim * sphase, bim = dre * sphase + dim * cphase;
+    const long long id = g.at(off, i, j);
+    for (int lev = 0; lev < 2; lev++) {
+        const double t = lev == 0 ? 0.0 : -S.ph.dt;
+        const double lon = (x - t - xc) / L;
+        const double env = mag * exp(-lon * lon);
+        typename Cplx<R>::t v;
+        v.x = (R)(bre * env);
+        v.y = (R)(bim * env);
+        S.f.a[S.d->abuf ^ lev][id] = v;
+    }
+}
+
+template <class R> __global__ void k_relocate(SimDev<R> S, int new_off) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const long long n = (long long)g.nlive * g.P;
+    const long long src0 = (long long)off * g.P, dst0 = (long long)new_off * g.P;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        S.f.ex[dst0 + k] = S.f.ex[src0 + k];
+        S.f.er[dst0 + k] = S.f.er[src0 + k];
+        S.f.bt[dst0 + k] = S.f.bt[src0 + k];
+        S.f.a[0][dst0 + k] = S.f.a[0][src0 + k];
+        S.f.a[1][dst0 + k] = S.f.a[1][src0 + k];
+    }
+}
+template <class R> __global__ void k_set_off(SimDev<R> S, int new_off) { S.d->off = new_off; }
+
+inline dim3 grid2(int nj, int ni) { return dim3((nj + BX - 1) / BX, (ni + BY - 1) / BY); }
+
+}  // namespace
+
+template <class R> void launch_prepass(const SimDev<R> &S, cudaStream_t st) {
+    k_prepass<R><<<grid2(S.geo.P, S.geo.nlive), dim3(BX, BY), 0, st>>>(S);
+}
+template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st) {
+    k_envelope<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);
+}
+template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st) {
+    k_ampere<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);
+}
+template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
+                                            double xc, double xf, cudaStream_t st) {
+    k_init_envelope<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S, a0, w0, L,
+                                                                                   xc, xf);
+}
+// Copies the live region of the persistent arrays to physical offset new_off (regions
+// must not overlap) and updates the descriptor.
+template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st) {
+    k_relocate<R><<<1216, 256, 0, st>>>(S, new_off);
+    k_set_off<R><<<1, 1, 0, st>>>(S, new_off);
+}
+
+#define INST(R)                                                                              \
+    template void launch_prepass<R>(const SimDev<R> &, cudaStream_t);                        \
+    template void launch_envelope<R>(const SimDev<R> &, cudaStream_t);                       \
+    template void launch_ampere<R>(const SimDev<R> &, cudaStream_t);                         \
+    template void launch_init_envelope<R>(const SimDev<R> &, double, double, double, double, \
+                                          double, cudaStream_t);                             \
+    template void launch_relocate<R>(const SimDev<R> &, int, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace lpic

@@ -1,0 +1,192 @@
+// Internal declarations of the lpic CUDA library (not part of the C ABI).
+//
+// Device data layout (one caller-owned buffer, sub-allocated by api.cu):
+//   * grid arrays: column-major in x ("r fastest"), column stride P >= nr+3 elements,
+//     kG guard columns on both sides of the live window, and a sliding physical column
+//     offset `off` so that a moving-window shift is a pointer slide plus the zeroing of
+//     the guard columns, not a copy of the grid (api.cu relocates the live region when
+//     the slide reaches the end of the allocation);
+//   * particles: structure of arrays, x kept as an int32 lab-frame cell index plus an
+//     in-cell offset in [0,1) of the working precision R, so the window shift never
+//     touches particles and FP32 keeps full resolution far from the origin.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lpic {
+
+constexpr int kG = 2;                    // guard columns on each side of the live window
+constexpr int32_t kDead = INT32_MIN;     // ix of a removed particle (a hole until compaction)
+constexpr double kPi = 3.14159265358979323846;
+
+enum ErrBits : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2 };
+
+// Device-resident per-simulation counters, read by every kernel so that a captured CUDA
+// graph replays correctly step after step.
+struct Desc {
+    long long step;    // n
+    long long shift;   // s: lab x of window column 0 is s*dx
+    int off;           // sliding physical column offset of the grid arrays
+    int np;            // particle slots in use (alive + holes)
+    int n_alive;       // alive count after the last compaction
+    int err;           // ErrBits, sticky
+    int abuf;          // index of the buffer holding A^n (the other holds A^{n-1})
+    int pbuf;          // index of the particle buffer in use (the other is the sort target)
+    int pad[6];
+};
+static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
+
+template <class R> struct Cplx;
+template <> struct Cplx<double> { using t = double2; };
+template <> struct Cplx<float> { using t = float2; };
+
+struct Geo {
+    int nx, nr;   // cells
+    int P;        // column stride in elements
+    int ncol;     // physical columns of every grid array
+    int nlive;    // nx + 1 + 2*kG columns of the live window (incl. guards)
+    __host__ __device__ __forceinline__ long long at(int off, int i, int j) const {
+        return (long long)(off + kG + i) * P + j;
+    }
+};
+
+template <class R> struct Fields {
+    R *ex, *er, *bt;                 // persistent: E^n, B^{n-1/2} -> B^{n+1/2}
+    typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
+    R *btn, *phi, *gx, *gr, *phih;   // per step: B^n, Phi^n, dPhi/dx, dPhi/dr, Phi^{n+1/2}
+    double *chi, *jx, *jr, *dq;      // per step FP64 accumulators
+};
+
+template <class R> struct Parts {
+    int32_t *ix;
+    R *ox, *y, *z, *px, *py, *pz, *w;
+    uint64_t *id;
+};
+
+struct Phys {
+    double dx, dr, dt;
+    int moving_window;
+    int have_plasma;
+    double n0, x_start, ramp_len;
+    int ppcx, ppcr, ppct;
+    unsigned long long seed;
+    int cap;
+    int track_dq;
+};
+
+template <class R> struct SimDev {
+    Geo geo;
+    Phys ph;
+    Desc *d;
+    Fields<R> f;
+    Parts<R> p[2];   // p[d->pbuf] in use; the counting sort scatters into the other
+};
+
+// ---- shared device helpers -------------------------------------------------------------
+__host__ __device__ __forceinline__ double plasma_density(const Phys &ph, double xlab) {
+    if (xlab < ph.x_start) return 0.0;
+    if (ph.ramp_len > 0.0 && xlab < ph.x_start + ph.ramp_len)
+        return ph.n0 * (xlab - ph.x_start) / ph.ramp_len;
+    return ph.n0;
+}
+
+// k-th output of SplitMix64 seeded with `seed` (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                                  unsigned long long k) {
+    unsigned long long z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Does the window shift after step n (window speed c)?  Same double arithmetic on host
+// and device.
+__host__ __device__ __forceinline__ bool window_shifts(const Phys &ph, long long n, long long s) {
+    return ph.moving_window && (double)(n + 1) * ph.dt >= (double)(s + 1) * ph.dx;
+}
+
+// Lattice particle of lab column c (paper Sec. 4 plasma sampling; regular ppc lattice):
+// local index enumerates (j, a valid, b, k); returns false if beyond the column's count.
+template <class R>
+__device__ __forceinline__ bool lattice_particle(const SimDev<R> &S, long long c, int local,
+                                                 int slot) {
+    const Phys &ph = S.ph;
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    int valid[16];
+    int nv = 0;
+    for (int a = 0; a < ph.ppcx && a < 16; a++) {
+        double xl = ((double)c + (a + 0.5) / ph.ppcx) * ph.dx;
+        if (plasma_density(ph, xl) > 0.0) valid[nv++] = a;
+    }
+    const int perj = nv * ph.ppcr * ph.ppct;
+    if (perj == 0 || local >= perj * S.geo.nr) return false;
+    const int j = local / perj;
+    int rem = local - j * perj;
+    const int av = rem / (ph.ppcr * ph.ppct);
+    rem -= av * ph.ppcr * ph.ppct;
+    const int b = rem / ph.ppct, kk = rem - b * ph.ppct;
+    const int a = valid[av];
+    const double xl = ((double)c + (a + 0.5) / ph.ppcx) * ph.dx;
+    const double n = plasma_density(ph, xl);
+    const double r = (j + (b + 0.5) / ph.ppcr) * ph.dr;
+    const unsigned long long cell = (unsigned long long)c * S.geo.nr + (unsigned long long)j;
+    const double u = (double)(splitmix64(ph.seed, cell + 1) >> 11) * (1.0 / 9007199254740992.0);
+    const double th = 2.0 * kPi * (kk + u) / ph.ppct;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    P.ix[slot] = (int)c;
+    P.ox[slot] = (R)((a + 0.5) / ph.ppcx);
+    P.y[slot] = (R)(r * cs);
+    P.z[slot] = (R)(r * sn);
+    P.px[slot] = (R)0;
+    P.py[slot] = (R)0;
+    P.pz[slot] = (R)0;
+    P.w[slot] = (R)(n * 2.0 * kPi * r * ph.dr * ph.dx / (ph.ppcx * ph.ppcr * ph.ppct));
+    P.id[slot] = ((cell * ph.ppcx + a) * ph.ppcr + b) * ph.ppct + kk;
+    return true;
+}
+
+// ---- launchers (defined in the kernel translation units) --------------------------------
+template <class R> void launch_prepass(const SimDev<R> &S, cudaStream_t st);
+template <class R> void launch_pass_a(const SimDev<R> &S, int np_upper, cudaStream_t st);
+template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st);
+template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st);
+template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st);
+template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st);
+template <class R> void launch_advance(const SimDev<R> &S, cudaStream_t st);
+
+template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
+                                            double xc, double xf, cudaStream_t st);
+template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_colbase, int ncols,
+                                            int total, cudaStream_t st);
+template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
+
+// counting sort by cell; `alt` receives the sorted particles; scratch ints:
+// key[cap], count[ncell+1], blocksum[...]
+template <class R> void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count,
+                                    int *blocksum, cudaStream_t st);
+
+// diagnostics (results in `out`, device doubles / uint64)
+template <class R> void launch_diag_ex_axis(const SimDev<R> &S, double *out, cudaStream_t st);
+template <class R> void launch_diag_amax_waist(const SimDev<R> &S, double *out3, cudaStream_t st);
+template <class R> void launch_diag_cont(const SimDev<R> &S, double *out2, cudaStream_t st);
+template <class R> void launch_diag_accel(const SimDev<R> &S, int np_upper, double thr,
+                                          double *out4, cudaStream_t st);
+// canonical dump / upload of one grid array (kind as in lpic_diag_kind), columns [c0, c1)
+template <class R> void launch_dump_field(const SimDev<R> &S, int kind, int c0, int c1,
+                                          double *stage, cudaStream_t st);
+template <class R> void launch_upload_field(const SimDev<R> &S, int kind, int c0, int c1,
+                                            const double *stage, cudaStream_t st);
+// alive-particle compaction index list (deterministic order); returns count via *d_count
+template <class R> void launch_alive_index(const SimDev<R> &S, int np_upper, int *idx,
+                                           int *blockcnt, int *d_count, cudaStream_t st);
+template <class R> void launch_dump_particles(const SimDev<R> &S, const int *idx, int k0, int k1,
+                                              int comp, double *stage, cudaStream_t st);
+template <class R> void launch_upload_particles(const SimDev<R> &S, int k0, int k1, int comp,
+                                                const double *stage, cudaStream_t st);
+template <class R> void launch_set_ids(const SimDev<R> &S, const int *idx, int k0, int k1,
+                                       const uint64_t *stage, uint64_t *out, int mode,
+                                       cudaStream_t st);
+template <class R> void launch_finish_upload(const SimDev<R> &S, int n, cudaStream_t st);
+
+}  // namespace lpic

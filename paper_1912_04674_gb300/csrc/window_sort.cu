@@ -1,0 +1,242 @@
+// Moving window (shift bookkeeping, guard zeroing, plasma injection at the front), step
+// counter advance, and the periodic counting sort of particles by cell.
+#include "lpic_internal.cuh"
+
+namespace lpic {
+
+namespace {
+
+constexpr int TPB = 256;
+
+// After step n: if the window shifts (paper Sec. 4 runs use a window moving at c), the live
+// window slides one physical column, the guard columns of the persistent arrays on both
+// sides of the new window are zeroed (the new front column of A and Er is among them), and
+// the new last cell column is filled with the plasma lattice at slots [np, np+count).
+template <class R> __global__ void k_window(SimDev<R> S) {
+    const long long n = S.d->step, s = S.d->shift;
+    if (!window_shifts(S.ph, n, s)) return;
+    const Geo g = S.geo;
+    const int noff = S.d->off + 1;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    // columns i in [-kG, -1] and [nx, nx+kG] of the new window
+    const int ncz = 2 * kG + 1;
+    for (int t = tid; t < ncz * g.P; t += nth) {
+        const int c = t / g.P, j = t - c * g.P;
+        const int i = c < kG ? c - kG : g.nx + (c - kG);
+        const long long id = g.at(noff, i, j);
+        S.f.ex[id] = (R)0;
+        S.f.er[id] = (R)0;
+        S.f.bt[id] = (R)0;
+        typename Cplx<R>::t zc;
+        zc.x = (R)0;
+        zc.y = (R)0;
+        S.f.a[0][id] = zc;
+        S.f.a[1][id] = zc;
+    }
+    if (!S.ph.have_plasma) return;
+    const long long c = s + 1 + g.nx - 1;  // lab column of the new last cell column
+    int nv = 0;
+    for (int a = 0; a < S.ph.ppcx; a++)
+        if (plasma_density(S.ph, ((double)c + (a + 0.5) / S.ph.ppcx) * S.ph.dx) > 0.0) nv++;
+    const int count = nv * S.ph.ppcr * S.ph.ppct * g.nr;
+    const int np = S.d->np;
+    if (np + count > S.ph.cap) {
+        if (tid == 0) atomicOr(&S.d->err, (int)ERR_CAPACITY);
+        return;
+    }
+    for (int t = tid; t < count; t += nth) lattice_particle<R>(S, c, t, np + t);
+}
+
+// Advance the counters after the window kernel (a separate launch, so that every thread of
+// the window kernel saw the same counters).
+template <class R> __global__ void k_advance(SimDev<R> S) {
+    Desc *d = S.d;
+    const long long n = d->step, s = d->shift;
+    if (window_shifts(S.ph, n, s)) {
+        if (S.ph.have_plasma && !(d->err & ERR_CAPACITY)) {
+            const long long c = s + S.geo.nx;
+            int nv = 0;
+            for (int a = 0; a < S.ph.ppcx; a++)
+                if (plasma_density(S.ph, ((double)c + (a + 0.5) / S.ph.ppcx) * S.ph.dx) > 0.0) nv++;
+            d->np += nv * S.ph.ppcr * S.ph.ppct * S.geo.nr;
+        }
+        d->shift = s + 1;
+        d->off += 1;
+    }
+    d->step = n + 1;
+    d->abuf ^= 1;
+}
+
+// ---- counting sort by window cell (x-major, r fastest, like the grid) -------------------
+template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *count) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const int np = S.d->np;
+    const long long s = S.d->shift;
+    const int ncell = S.geo.nx * S.geo.nr;
+    const double idr = 1.0 / S.ph.dr;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        const int ix = P.ix[k];
+        int c;
+        if (ix == kDead) {
+            c = ncell;
+        } else {
+            const double y = (double)P.y[k], z = (double)P.z[k];
+            int j = (int)(sqrt(y * y + z * z) * idr);
+            j = min(max(j, 0), S.geo.nr - 1);
+            int i = (int)((long long)ix - s);
+            i = min(max(i, 0), S.geo.nx - 1);
+            c = i * S.geo.nr + j;
+        }
+        key[k] = c;
+        atomicAdd(count + c, 1);
+    }
+}
+
+// Exclusive scan of count[0..n) in place, three phases over blocks of 4096 items.
+constexpr int SB = 1024, SI = 4;
+__device__ __forceinline__ int block_exclusive_scan(int v, int *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (SB / 32) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    const int before = wid > 0 ? sh[wid - 1] : 0;
+    const int total = sh[SB / 32 - 1];
+    __syncthreads();
+    sh[32] = total;
+    return before + x - v;
+}
+
+__global__ void k_scan_blocks(int *data, int n, int *blocksum) {
+    __shared__ int sh[40];
+    const int base = blockIdx.x * SB * SI + threadIdx.x * SI;
+    int v[SI], tsum = 0;
+#pragma unroll
+    for (int q = 0; q < SI; q++) {
+        v[q] = base + q < n ? data[base + q] : 0;
+        tsum += v[q];
+    }
+    int ex = block_exclusive_scan(tsum, sh);
+#pragma unroll
+    for (int q = 0; q < SI; q++) {
+        if (base + q < n) data[base + q] = ex;
+        ex += v[q];
+    }
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = sh[32];
+}
+
+__global__ void k_scan_top(int *blocksum, int nb) {  // one block, nb <= SB*SI
+    __shared__ int sh[40];
+    const int base = threadIdx.x * SI;
+    int v[SI], tsum = 0;
+#pragma unroll
+    for (int q = 0; q < SI; q++) {
+        v[q] = base + q < nb ? blocksum[base + q] : 0;
+        tsum += v[q];
+    }
+    int ex = block_exclusive_scan(tsum, sh);
+#pragma unroll
+    for (int q = 0; q < SI; q++) {
+        if (base + q < nb) blocksum[base + q] = ex;
+        ex += v[q];
+    }
+}
+
+__global__ void k_scan_add(int *data, int n, const int *blocksum) {
+    const int b = blockIdx.x, add = blocksum[b];
+    const int base = b * SB * SI + threadIdx.x * SI;
+#pragma unroll
+    for (int q = 0; q < SI; q++)
+        if (base + q < n) data[base + q] += add;
+}
+
+template <class R>
+__global__ void k_sort_scatter(SimDev<R> S, const int *key, int *cursor) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const Parts<R> out = S.d->pbuf ? S.p[0] : S.p[1];
+    const int np = S.d->np;
+    const int ncell = S.geo.nx * S.geo.nr;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        const int c = key[k];
+        if (c == ncell) continue;  // dead: dropped
+        const int d = atomicAdd(cursor + c, 1);
+        out.ix[d] = P.ix[k];
+        out.ox[d] = P.ox[k];
+        out.y[d] = P.y[k];
+        out.z[d] = P.z[k];
+        out.px[d] = P.px[k];
+        out.py[d] = P.py[k];
+        out.pz[d] = P.pz[k];
+        out.w[d] = P.w[k];
+        out.id[d] = P.id[k];
+    }
+}
+
+// After the scatter cursor[c] = end of cell c, so cursor[ncell-1] is the alive count.
+template <class R> __global__ void k_sort_finish(SimDev<R> S, const int *cursor) {
+    const int ncell = S.geo.nx * S.geo.nr;
+    const int alive = ncell > 0 ? cursor[ncell - 1] : 0;
+    S.d->np = alive;
+    S.d->n_alive = alive;
+    S.d->pbuf ^= 1;
+}
+
+inline int pgrid(int n) {
+    int b = (n + TPB - 1) / TPB;
+    return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
+}
+
+}  // namespace
+
+template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st) {
+    int work = (2 * kG + 1) * S.geo.P;
+    if (inj_upper > work) work = inj_upper;
+    k_window<R><<<pgrid(work), TPB, 0, st>>>(S);
+}
+template <class R> void launch_advance(const SimDev<R> &S, cudaStream_t st) {
+    k_advance<R><<<1, 1, 0, st>>>(S);
+}
+
+// Exclusive scan of n <= SB*SI*SB*SI ints in place.
+void scan_exclusive(int *data, int n, int *blocksum, cudaStream_t st) {
+    const int per = SB * SI;
+    const int nb = (n + per - 1) / per;
+    k_scan_blocks<<<nb, SB, 0, st>>>(data, n, blocksum);
+    k_scan_top<<<1, SB, 0, st>>>(blocksum, nb);
+    k_scan_add<<<nb, SB, 0, st>>>(data, n, blocksum);
+}
+
+template <class R>
+void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count, int *blocksum,
+                 cudaStream_t st) {
+    const int ncell = S.geo.nx * S.geo.nr;
+    cudaMemsetAsync(count, 0, sizeof(int) * (ncell + 1), st);
+    k_sort_count<R><<<pgrid(np_upper), TPB, 0, st>>>(S, key, count);
+    scan_exclusive(count, ncell + 1, blocksum, st);
+    k_sort_scatter<R><<<pgrid(np_upper), TPB, 0, st>>>(S, key, count);
+    k_sort_finish<R><<<1, 1, 0, st>>>(S, count);
+}
+
+#define INST(R)                                                                          \
+    template void launch_window<R>(const SimDev<R> &, int, cudaStream_t);                \
+    template void launch_advance<R>(const SimDev<R> &, cudaStream_t);                    \
+    template void launch_sort<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace lpic

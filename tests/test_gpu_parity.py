@@ -1,0 +1,141 @@
+"""FP64 CUDA path against the FP64 oracle, through the C ABI, on the same seeded inputs.
+
+Bar: after every compared step each field and each particle component agrees with the oracle
+to 1e-10 relative in the max norm (atomic deposit order and FMA contraction are the only
+differences; both are O(1e-16) per operation).  Particles are matched by id.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from helpers import (field_errors, gpu_from, oracle_from, oracle_state_to_gpu, particle_errors,
+                     rel_err)
+from workloads import C1
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1912_04674_gb300 import build
+    build.build()
+
+
+def assert_parity(o, sim, tol=TOL, names=None):
+    fe = field_errors(o, sim) if names is None else field_errors(o, sim, names)
+    pe = particle_errors(o, sim) if o.np else {}
+    bad = {k: v for k, v in {**fe, **pe}.items() if not v <= tol}
+    assert not bad, bad
+    return fe, pe
+
+
+def test_first_step_c1_full_size():
+    o = oracle_from(C1)
+    g = gpu_from(C1)
+    assert g.counters()["alive"] == o.np == C1.particles
+    assert_parity(o, g)           # initial lattice and envelope
+    o.step(1)
+    g.step(1)
+    assert_parity(o, g)
+
+
+def test_free_run_c1_forty_steps_with_sorting():
+    w = dataclasses.replace(C1, sort_every=4)
+    o = oracle_from(w)
+    g = gpu_from(w)
+    for n in (1, 9, 30):
+        o.step(n)
+        g.step(n)
+        fe, pe = assert_parity(o, g, tol=1e-9)
+    assert g.counters()["shift"] == o.shift > 0
+
+
+def test_one_step_from_oracle_state_after_25_steps():
+    o = oracle_from(C1)
+    o.step(25)
+    g = gpu_from(C1)
+    oracle_state_to_gpu(o, g)
+    assert_parity(o, g, names=("ex", "er", "bt", "a", "am"))
+    for _ in range(2):
+        o.step(1)
+        g.step(1)
+        assert_parity(o, g)
+
+
+@pytest.mark.parametrize("nx,nr,ppc", [(37, 23, (2, 2, 4)), (50, 9, (1, 3, 2)), (129, 33, (3, 1, 1))])
+def test_ragged_grids_moving_window_and_injection(nx, nr, ppc):
+    w = dataclasses.replace(C1, name="ragged", nx=nx, nr=nr, ppc=ppc, a0=0.5, w0=8.0, L=6.0,
+                            n0=0.01, ramp_cells=7, sort_every=3)
+    o = oracle_from(w)
+    g = gpu_from(w)
+    for _ in range(4):
+        o.step(3)
+        g.step(3)
+        assert_parity(o, g, tol=1e-9)
+    assert o.shift >= 9
+
+
+def test_vacuum_envelope_and_waist_no_particles():
+    w = dataclasses.replace(C1, name="vacuum", nx=96, nr=48, w0=15.0, L=10.0, a0=1.0)
+    o = oracle_from(w, plasma=False)
+    g = gpu_from(w, plasma=False)
+    o.step(60)
+    g.step(60)
+    assert_parity(o, g, names=("a", "am", "ex", "er", "bt"))
+    A = o.field("a")
+    r = np.arange(w.nr + 1) * w.dr
+    v = r * w.dr
+    v[0] = w.dr * w.dr / 8
+    inten = np.abs(A) ** 2
+    waist = np.sqrt(2 * (inten * r ** 2 * v).sum() / (inten * v).sum())
+    assert abs(g.waist() / waist - 1) < 1e-12
+    assert abs(g.a_abs_max() / np.abs(A).max() - 1) < 1e-12
+
+
+def test_diagnostics_match_oracle_state():
+    from paper_1912_04674_gb300 import lpic as L
+    w = dataclasses.replace(C1, name="diag", nx=64, nr=32, a0=1.0, w0=12.0, L=8.0, n0=0.01)
+    thr = 0.01
+    o = oracle_from(w)
+    gt = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every, track_continuity=True,
+                accel_px_min=thr)
+    g = L.Simulation(gt, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
+                     L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed))
+    o.step(40)
+    g.step(40)
+    assert rel_err(g.ex_axis(), o.field("ex")[:, 0]) < 1e-9
+    c = g.counters()
+    assert c["alive"] == o.np and c["step"] == 40 and c["shift"] == o.shift
+    res = g.cont_residual()
+    assert res < 1e-12, res
+    # accelerated-electron statistics against numpy on the oracle state
+    p = o.particles()
+    sel = p["px"] > thr
+    gam = np.sqrt(1 + p["px"] ** 2 + p["py"] ** 2 + p["pz"] ** 2) - 1
+    cnt, sw, mean, rms = g.accel_energy()
+    assert cnt == sel.sum() and cnt > 0
+    ww = p["w"][sel]
+    m = (ww * gam[sel]).sum() / ww.sum()
+    assert abs(sw / ww.sum() - 1) < 1e-9
+    assert abs(mean / m - 1) < 1e-8
+    assert abs(rms - np.sqrt((ww * (gam[sel] - m) ** 2).sum() / ww.sum())) < 1e-8 * m
+
+
+def test_errors_are_reported_not_faulted():
+    from paper_1912_04674_gb300 import lpic as L
+    w = dataclasses.replace(C1, nx=32, nr=16)
+    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, 4)
+    with pytest.raises(L.LpicError) as e:          # capacity far too small for the lattice
+        L.Simulation(g, None, L.Plasma(0.001), capacity=100)
+    assert e.value.status == 4
+    sim = L.Simulation(g, None, None, capacity=0)
+    with pytest.raises(L.LpicError) as e:          # continuity tracking is off
+        sim.cont_residual()
+    assert e.value.status == 8
+    with pytest.raises(L.LpicError) as e:          # wrong upload size
+        sim.upload_field("ex", np.zeros((3, 3)))
+    assert e.value.status == 1
+    sim.step(3)                                    # vacuum, no particles: still runs
+    assert sim.counters()["step"] == 3
