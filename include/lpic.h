@@ -99,6 +99,8 @@ typedef enum {
     LPIC_DIAG_A = 13,            /* A^n, complex (re,im)                                     */
     LPIC_DIAG_AM = 14,           /* A^{n-1}, complex (re,im)                                 */
     LPIC_DIAG_CHI = 15, LPIC_DIAG_JX = 16, LPIC_DIAG_JR = 17, LPIC_DIAG_DQ = 18,
+                                 /* chi, J, dQ: deposits of the last step, on that step's window
+                                    (before its moving-window shift)                        */
     LPIC_DIAG_PARTICLES = 20,    /* 7 x n doubles, SoA: x(lab), y, z, px, py, pz, w          */
     LPIC_DIAG_PARTICLE_IDS = 21  /* n uint64 ids, same order as LPIC_DIAG_PARTICLES          */
 } lpic_diag_kind;

@@ -46,9 +46,12 @@ typedef struct osim {
     double *dq;                          /* charge change of the last step (diagnostic) */
     /* node scratch */
     double *phi, *dphix, *dphir, *phih;
-    /* particles */
+    /* particles: x is kept as the lab cell index ix and the in-cell offset ox in [0,1)
+     * (x_lab = (ix + ox) dx), so that a displacement is never lost against the size of
+     * the lab coordinate */
     long np, cap;
-    double *x, *y, *z, *px, *py, *pz, *w;
+    long *ix;
+    double *ox, *y, *z, *px, *py, *pz, *w;
     uint64_t *id;
     /* plasma profile kept for injection at the moving window front */
     int have_plasma;
@@ -93,7 +96,7 @@ void osim_free(osim *s)
     free(s->ex); free(s->jx); free(s->er); free(s->jr); free(s->bt); free(s->btn);
     free(s->a); free(s->am); free(s->chi); free(s->dq);
     free(s->phi); free(s->dphix); free(s->dphir); free(s->phih);
-    free(s->x); free(s->y); free(s->z); free(s->px); free(s->py); free(s->pz);
+    free(s->ix); free(s->ox); free(s->y); free(s->z); free(s->px); free(s->py); free(s->pz);
     free(s->w); free(s->id);
     free(s);
 }
@@ -102,7 +105,8 @@ void osim_free(osim *s)
 void osim_reserve(osim *s, long cap)
 {
     if (cap <= s->cap) return;
-    s->x = realloc(s->x, cap * sizeof(double));
+    s->ix = realloc(s->ix, cap * sizeof(long));
+    s->ox = realloc(s->ox, cap * sizeof(double));
     s->y = realloc(s->y, cap * sizeof(double));
     s->z = realloc(s->z, cap * sizeof(double));
     s->px = realloc(s->px, cap * sizeof(double));
@@ -120,11 +124,11 @@ void osim_set_np(osim *s, long np)
     s->np = np;
 }
 
-static void push_particle(osim *s, double x, double y, double z, double w, uint64_t id)
+static void push_particle(osim *s, long ix, double ox, double y, double z, double w, uint64_t id)
 {
     if (s->np == s->cap) osim_reserve(s, s->cap ? 2 * s->cap : 1024);
     long k = s->np++;
-    s->x[k] = x; s->y[k] = y; s->z[k] = z;
+    s->ix[k] = ix; s->ox[k] = ox; s->y[k] = y; s->z[k] = z;
     s->px[k] = 0.0; s->py[k] = 0.0; s->pz[k] = 0.0;
     s->w[k] = w; s->id[k] = id;
 }
@@ -188,7 +192,8 @@ static void load_column(osim *s, long c)
         uint64_t cell = (uint64_t)c * (uint64_t)s->nr + (uint64_t)j;
         double u = (double)(osim_splitmix64(s->seed, cell + 1) >> 11) * (1.0 / 9007199254740992.0);
         for (int a = 0; a < s->ppcx; a++) {
-            double xlab = (c + (a + 0.5) / s->ppcx) * s->dx;
+            double frac = (a + 0.5) / s->ppcx;
+            double xlab = (c + frac) * s->dx;
             double n = density(s, xlab);
             if (n <= 0.0) continue;
             for (int b = 0; b < s->ppcr; b++) {
@@ -197,7 +202,7 @@ static void load_column(osim *s, long c)
                 for (int k = 0; k < s->ppct; k++) {
                     double th = 2.0 * PI * (k + u) / s->ppct;
                     uint64_t pid = ((cell * s->ppcx + a) * s->ppcr + b) * s->ppct + k;
-                    push_particle(s, xlab, r * cos(th), r * sin(th), w, pid);
+                    push_particle(s, c, frac, r * cos(th), r * sin(th), w, pid);
                 }
             }
         }
@@ -276,16 +281,20 @@ static double grid_at(const double *F, int ni, int nj, int i, int j, int odd_r)
 }
 
 static double gather(const double *F, int ni, int nj, double sx, double sr,
-                     double xn, double rn)
+                     long icell, double fcell, double rn)
 {
-    double u = xn - sx, v = rn - sr;
-    int i0 = (int)floor(u), j0 = (int)floor(v);
-    double fu = u - i0, fv = v - j0;
+    /* x position = icell + fcell (window cells), fcell in [0,1) */
+    double u = fcell - sx;
+    long i0 = icell;
+    if (u < 0.0) { u += 1.0; i0 -= 1; }
+    double v = rn - sr;
+    int j0 = (int)floor(v);
+    double fu = u, fv = v - j0;
     int odd = (sr != 0.0);
-    return (1.0 - fu) * (1.0 - fv) * grid_at(F, ni, nj, i0, j0, odd)
-         + fu * (1.0 - fv) * grid_at(F, ni, nj, i0 + 1, j0, odd)
-         + (1.0 - fu) * fv * grid_at(F, ni, nj, i0, j0 + 1, odd)
-         + fu * fv * grid_at(F, ni, nj, i0 + 1, j0 + 1, odd);
+    return (1.0 - fu) * (1.0 - fv) * grid_at(F, ni, nj, (int)i0, j0, odd)
+         + fu * (1.0 - fv) * grid_at(F, ni, nj, (int)(i0 + 1), j0, odd)
+         + (1.0 - fu) * fv * grid_at(F, ni, nj, (int)i0, j0 + 1, odd)
+         + fu * fv * grid_at(F, ni, nj, (int)(i0 + 1), j0 + 1, odd);
 }
 
 /* Node volumes.  Ring volume 2 pi r_j dr dx for j>=1.  The axis node:
@@ -341,21 +350,22 @@ void osim_pass_a(osim *s)
 {
     int nx = s->nx, nr = s->nr;
     const double q = -1.0;
-    double x0 = s->shift * s->dx, hdt = 0.5 * s->dt;
+    double hdt = 0.5 * s->dt;
     ponderomotive_nodes(s);
     memset(s->chi, 0, n_node(s) * sizeof(double));
     for (long k = 0; k < s->np; k++) {
-        double xn = (s->x[k] - x0) / s->dx;
+        long ic = s->ix[k] - s->shift;
+        double fx = s->ox[k];
         double r = sqrt(s->y[k] * s->y[k] + s->z[k] * s->z[k]);
         double rn = r / s->dr;
         double ct = 1.0, st = 0.0;
         if (r > 0.0) { ct = s->y[k] / r; st = s->z[k] / r; }
-        double exg = gather(s->ex, nx, nr + 1, 0.5, 0.0, xn, rn);
-        double erg = gather(s->er, nx + 1, nr, 0.0, 0.5, xn, rn);
-        double btg = gather(s->btn, nx, nr, 0.5, 0.5, xn, rn);
-        double phg = gather(s->phi, nx + 1, nr + 1, 0.0, 0.0, xn, rn);
-        double gxg = gather(s->dphix, nx + 1, nr + 1, 0.0, 0.0, xn, rn);
-        double grg = gather(s->dphir, nx + 1, nr + 1, 0.0, 0.0, xn, rn);
+        double exg = gather(s->ex, nx, nr + 1, 0.5, 0.0, ic, fx, rn);
+        double erg = gather(s->er, nx + 1, nr, 0.0, 0.5, ic, fx, rn);
+        double btg = gather(s->btn, nx, nr, 0.5, 0.5, ic, fx, rn);
+        double phg = gather(s->phi, nx + 1, nr + 1, 0.0, 0.0, ic, fx, rn);
+        double gxg = gather(s->dphix, nx + 1, nr + 1, 0.0, 0.0, ic, fx, rn);
+        double grg = gather(s->dphir, nx + 1, nr + 1, 0.0, 0.0, ic, fx, rn);
         double E[3] = {exg, erg * ct, erg * st};
         double B[3] = {0.0, -btg * st, btg * ct};
         double G[3] = {gxg, grg * ct, grg * st};
@@ -367,8 +377,8 @@ void osim_pass_a(osim *s)
         double gt = sqrt(1.0 + ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2] + phg);
 
         /* susceptibility deposit with the primal linear weights */
-        int i0 = (int)floor(xn), j0 = (int)floor(rn);
-        double fx = xn - i0, fr = rn - j0;
+        int i0 = (int)ic, j0 = (int)floor(rn);
+        double fr = rn - j0;
         for (int di = 0; di < 2; di++)
             for (int dj = 0; dj < 2; dj++) {
                 int i = i0 + di, j = j0 + dj;
@@ -453,11 +463,15 @@ void osim_envelope(osim *s)
  * so that dQ/dt + (Ix_{i+1/2}-Ix_{i-1/2}) + (Ir_{j+1/2}-Ir_{j-1/2}) = 0 node by node.
  * Contributions to points outside the grid are discarded.  The charge change
  * q w DS is also recorded (diagnostic of the continuity residual).
+ *
+ * DS is a difference of shape factors at two nearby positions, so both positions are
+ * taken relative to the particle's cell: x as (cell, offset) moved by dt v_x/dx, and the
+ * new radius as r^n + dr_step with the radial step in the cancellation-free form
+ *   dr_step = (dy (y^n + y^{n+1}) + dz (z^n + z^{n+1})) / (r^n + r^{n+1}),
+ * dy = dt p_y/gbar, dz = dt p_z/gbar (the identity r1^2 - r0^2 = (r1 - r0)(r1 + r0)).
  */
-static void shape3(double xn, int base, double out[3])
+static void shape3(long i0, double f, long base, double out[3])
 {
-    int i0 = (int)floor(xn);
-    double f = xn - i0;
     out[0] = out[1] = out[2] = 0.0;
     out[i0 - base] = 1.0 - f;
     out[i0 - base + 1] = f;
@@ -467,7 +481,7 @@ void osim_pass_b(osim *s)
 {
     int nx = s->nx, nr = s->nr;
     const double q = -1.0;
-    double x0 = s->shift * s->dx, dt = s->dt;
+    double dt = s->dt;
     for (long k = 0; k < n_node(s); k++)
         s->phih[k] = 0.5 * (0.5 * (creal(s->a[k]) * creal(s->a[k]) + cimag(s->a[k]) * cimag(s->a[k]))
                           + 0.5 * (creal(s->am[k]) * creal(s->am[k]) + cimag(s->am[k]) * cimag(s->am[k])));
@@ -475,24 +489,36 @@ void osim_pass_b(osim *s)
     memset(s->jr, 0, n_er(s) * sizeof(double));
     memset(s->dq, 0, n_node(s) * sizeof(double));
     for (long k = 0; k < s->np; k++) {
-        double xn0 = (s->x[k] - x0) / s->dx;
-        double r0 = sqrt(s->y[k] * s->y[k] + s->z[k] * s->z[k]);
+        long ia = s->ix[k] - s->shift;
+        double fa = s->ox[k];
+        double y0 = s->y[k], z0 = s->z[k];
+        double r0 = sqrt(y0 * y0 + z0 * z0);
         double rn0 = r0 / s->dr;
-        double ph = gather(s->phih, nx + 1, nr + 1, 0.0, 0.0, xn0, rn0);
+        double ph = gather(s->phih, nx + 1, nr + 1, 0.0, 0.0, ia, fa, rn0);
         double p2 = s->px[k] * s->px[k] + s->py[k] * s->py[k] + s->pz[k] * s->pz[k];
         double gbar = sqrt(1.0 + p2 + ph);
-        s->x[k] += dt * s->px[k] / gbar;
-        s->y[k] += dt * s->py[k] / gbar;
-        s->z[k] += dt * s->pz[k] / gbar;
-        double xn1 = (s->x[k] - x0) / s->dx;
-        double rn1 = sqrt(s->y[k] * s->y[k] + s->z[k] * s->z[k]) / s->dr;
+        double ddx = dt * s->px[k] / gbar, ddy = dt * s->py[k] / gbar, ddz = dt * s->pz[k] / gbar;
+        /* x: offset push within the cell frame */
+        double fb = fa + ddx / s->dx;
+        long ib = ia + (long)floor(fb);
+        fb -= floor(fb);
+        s->ix[k] += ib - ia;
+        s->ox[k] = fb;
+        /* r: new radius from the radial step */
+        double y1 = y0 + ddy, z1 = z0 + ddz;
+        double r1 = sqrt(y1 * y1 + z1 * z1);
+        double step_r = (r0 + r1 > 0.0) ? (ddy * (y0 + y1) + ddz * (z0 + z1)) / (r0 + r1) : 0.0;
+        double rn1 = rn0 + step_r / s->dr;
+        if (rn1 < 0.0) rn1 = 0.0;
+        s->y[k] = y1;
+        s->z[k] = z1;
 
-        int ia = (int)floor(xn0), ib = (int)floor(xn1);
         int ja = (int)floor(rn0), jb = (int)floor(rn1);
-        int imin = ia < ib ? ia : ib, jmin = ja < jb ? ja : jb;
+        long imin = ia < ib ? ia : ib;
+        int jmin = ja < jb ? ja : jb;
         double s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
-        shape3(xn0, imin, s0x); shape3(xn1, imin, s1x);
-        shape3(rn0, jmin, s0r); shape3(rn1, jmin, s1r);
+        shape3(ia, fa, imin, s0x); shape3(ib, fb, imin, s1x);
+        shape3(ja, rn0 - ja, jmin, s0r); shape3(jb, rn1 - jb, jmin, s1r);
         for (int c = 0; c < 3; c++) { dsx[c] = s1x[c] - s0x[c]; dsr[c] = s1r[c] - s0r[c]; }
         double qw = q * s->w[k];
         for (int l = 0; l < 3; l++) {          /* Jx on faces imin+1/2, imin+3/2 */
@@ -500,14 +526,14 @@ void osim_pass_b(osim *s)
             double acc = 0.0;
             for (int c = 0; c < 2; c++) {
                 acc += dsx[c] * (s0r[l] + 0.5 * dsr[l]);
-                int i = imin + c;
+                long i = imin + c;
                 if (i < 0 || i >= nx || j < 0 || j > nr) continue;
                 double area = vol_q(s, j) / s->dx;
                 s->jx[i * (nr + 1) + j] += -qw / dt * acc / area;
             }
         }
         for (int c = 0; c < 3; c++) {          /* Jr on faces jmin+1/2, jmin+3/2 */
-            int i = imin + c;
+            long i = imin + c;
             double acc = 0.0;
             for (int l = 0; l < 2; l++) {
                 acc += dsr[l] * (s0x[c] + 0.5 * dsx[c]);
@@ -519,7 +545,8 @@ void osim_pass_b(osim *s)
         }
         for (int c = 0; c < 3; c++)
             for (int l = 0; l < 3; l++) {
-                int i = imin + c, j = jmin + l;
+                long i = imin + c;
+                int j = jmin + l;
                 if (i < 0 || i > nx || j < 0 || j > nr) continue;
                 s->dq[i * (nr + 1) + j] += qw * (s1x[c] * s1r[l] - s0x[c] * s0r[l]);
             }
@@ -557,13 +584,14 @@ void osim_window(osim *s)
         shift_carray(s->am, nx + 1, nr + 1);
         if (s->have_plasma) load_column(s, s->shift + nx - 1);
     }
-    double x0 = s->shift * s->dx, xmax = nx * s->dx, rmax = nr * s->dr;
+    double rmax = nr * s->dr;
     long keep = 0;
     for (long k = 0; k < s->np; k++) {
-        double xr = s->x[k] - x0;
+        long ic = s->ix[k] - s->shift;
         double r = sqrt(s->y[k] * s->y[k] + s->z[k] * s->z[k]);
-        if (xr < 0.0 || xr >= xmax || r >= rmax) continue;
-        s->x[keep] = s->x[k]; s->y[keep] = s->y[k]; s->z[keep] = s->z[k];
+        if (ic < 0 || ic >= nx || r >= rmax) continue;
+        s->ix[keep] = s->ix[k]; s->ox[keep] = s->ox[k];
+        s->y[keep] = s->y[k]; s->z[keep] = s->z[k];
         s->px[keep] = s->px[k]; s->py[keep] = s->py[k]; s->pz[keep] = s->pz[k];
         s->w[keep] = s->w[k]; s->id[keep] = s->id[k];
         keep++;
@@ -604,11 +632,25 @@ enum { P_X = 0, P_Y, P_Z, P_PX, P_PY, P_PZ, P_W, P_ID };
 void *osim_particles(osim *s, int which)
 {
     switch (which) {
-    case P_X: return s->x;   case P_Y: return s->y;   case P_Z: return s->z;
+    case P_X: return 0;      case P_Y: return s->y;   case P_Z: return s->z;
     case P_PX: return s->px; case P_PY: return s->py; case P_PZ: return s->pz;
     case P_W: return s->w;   case P_ID: return s->id;
     }
     return 0;
+}
+/* Lab-frame x of every particle, (ix + ox) dx, and its inverse. */
+void osim_get_x(const osim *s, double *out)
+{
+    for (long k = 0; k < s->np; k++) out[k] = ((double)s->ix[k] + s->ox[k]) * s->dx;
+}
+void osim_set_x(osim *s, const double *in)
+{
+    for (long k = 0; k < s->np; k++) {
+        double u = in[k] / s->dx, f = floor(u);
+        s->ix[k] = (long)f;
+        s->ox[k] = u - f;
+        if (s->ox[k] >= 1.0) { s->ox[k] = 0.0; s->ix[k] += 1; }
+    }
 }
 long osim_np(const osim *s) { return s->np; }
 long osim_step_index(const osim *s) { return s->step; }

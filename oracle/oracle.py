@@ -68,6 +68,8 @@ def lib():
             L.osim_shift.argtypes = [vp]
             L.osim_set_np.argtypes = [vp, l]
             L.osim_set_counters.argtypes = [vp, l, l]
+            L.osim_get_x.argtypes = [vp, C.POINTER(d)]
+            L.osim_set_x.argtypes = [vp, C.POINTER(d)]
             L.osim_splitmix64.restype = u64
             L.osim_splitmix64.argtypes = [u64, u64]
             _lib = L
@@ -139,7 +141,13 @@ class OSim:
         self.L.osim_set_counters(self.h, int(step), int(shift))
 
     def part(self, name) -> np.ndarray:
+        """View of a particle component; "x" (lab frame) is a computed copy."""
         n = self.np
+        if name == "x":
+            out = np.empty(n)
+            if n:
+                self.L.osim_get_x(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
+            return out
         ptr = self.L.osim_particles(self.h, PARTS[name])
         if n == 0 or not ptr:
             return np.zeros(0, dtype=np.uint64 if name == "id" else np.float64)
@@ -155,7 +163,12 @@ class OSim:
             v = arrs.get(k)
             if v is None:
                 v = np.arange(n, dtype=np.uint64) if k == "id" else np.zeros(n)
-            if n:
+            if not n:
+                continue
+            if k == "x":
+                xv = np.ascontiguousarray(v, dtype=np.float64)
+                self.L.osim_set_x(self.h, xv.ctypes.data_as(C.POINTER(C.c_double)))
+            else:
                 self.part(k)[:] = v
 
     def particles(self) -> dict:

@@ -58,7 +58,7 @@ template <class R> __global__ void k_amax_waist(SimDev<R> S, double *out) {
 // out[0] = max |dQ/dt + div I|, out[1] = max |div I|, I = J times face area.
 template <class R> __global__ void k_cont(SimDev<R> S, double *out) {
     const Geo g = S.geo;
-    const int off = S.d->off;
+    const int off = S.d->off - S.d->last_shift;  // the window the last step deposited on
     const double dx = S.ph.dx, dr = S.ph.dr, dt = S.ph.dt;
     const long long n = (long long)(g.nx - 1) * g.nr;
     double rmax = 0.0, dmax = 0.0;
@@ -128,7 +128,8 @@ __host__ __device__ inline void kind_shape(int kind, int nx, int nr, int &ni, in
 template <class R> __global__ void k_dump_field(SimDev<R> S, int kind, int c0, int c1, double *st) {
     int ni, nj, cplx;
     kind_shape(kind, S.geo.nx, S.geo.nr, ni, nj, cplx);
-    const int off = S.d->off;
+    // per-step deposits (chi, J, dQ) are read on the window of the step that made them
+    const int off = S.d->off - (kind >= 15 ? S.d->last_shift : 0);
     const long long n = (long long)(c1 - c0) * nj;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {

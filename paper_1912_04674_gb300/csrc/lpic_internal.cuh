@@ -32,7 +32,9 @@ struct Desc {
     int err;           // ErrBits, sticky
     int abuf;          // index of the buffer holding A^n (the other holds A^{n-1})
     int pbuf;          // index of the particle buffer in use (the other is the sort target)
-    int pad[6];
+    int last_shift;    // 1 if the last step ended with a window shift (its deposits sit one
+                       // physical column before the current window)
+    int pad[5];
 };
 static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
 

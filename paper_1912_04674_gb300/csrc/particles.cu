@@ -171,8 +171,12 @@ template <class R> __global__ void __launch_bounds__(TPB) k_pass_b(SimDev<R> S) 
         const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
         const R gbar = sqrt((R)1 + px * px + py * py + pz * pz + ph);
         const R ig = (R)1 / gbar;
+        // The current is a difference of shape factors at two nearby positions: move x as
+        // an in-cell offset, and take the new radius as r^n plus the radial step in the
+        // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
         R ox1 = ox + dtdx * px * ig;
-        const R y1 = y + dt * py * ig, z1 = z + dt * pz * ig;
+        const R dy = dt * py * ig, dz = dt * pz * ig;
+        const R y1 = y + dy, z1 = z + dz;
         // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
         // keep the 3-node shape window in range for non-finite input
         int di = min(max((int)floor(ox1), -1), 1);
@@ -180,7 +184,10 @@ template <class R> __global__ void __launch_bounds__(TPB) k_pass_b(SimDev<R> S) 
         if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
         const int ia = L.ip, ib = L.ip + di;
         const R r1 = sqrt(y1 * y1 + z1 * z1);
-        const R rn1 = r1 * idr;
+        const R rsum = r0 + r1;
+        const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
+        R rn1 = rn0 + step_r * idr;
+        if (rn1 < (R)0) rn1 = (R)0;
         const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
         const R fra = L.gp, frb = rn1 - (R)jb;
         const int imin = min(ia, ib), jmin = min(ja, jb);

@@ -52,7 +52,8 @@ template <class R> __global__ void k_window(SimDev<R> S) {
 template <class R> __global__ void k_advance(SimDev<R> S) {
     Desc *d = S.d;
     const long long n = d->step, s = d->shift;
-    if (window_shifts(S.ph, n, s)) {
+    d->last_shift = window_shifts(S.ph, n, s) ? 1 : 0;
+    if (d->last_shift) {
         if (S.ph.have_plasma && !(d->err & ERR_CAPACITY)) {
             const long long c = s + S.geo.nx;
             int nv = 0;
