@@ -171,6 +171,27 @@ lpic_status lpic_set_kernel_timing(lpic_ctx *ctx, int enable);
 lpic_status lpic_kernel_stats(lpic_ctx *ctx, int64_t *launches, double *ms, int cap, int *n);
 const char *lpic_kernel_name(int k);
 
+/* Allocation-free envelope statistics.  The paper has no counterpart: this is a service for
+ * callers that cannot call cudaMalloc -- code whose device memory all comes from a pool it
+ * was handed (a host framework with its own allocator, a plug-in, a real-time loop whose
+ * memory is fixed before it starts) -- and so cannot create a context either.
+ * Computes, like lpic_diagnose(LPIC_DIAG_A_ABS_MAX) and lpic_diagnose(LPIC_DIAG_WAIST),
+ *   out_dev[0] = max |A|,  out_dev[1] = sqrt(2 <r^2>) weighted by |A|^2 (node volumes),
+ * from a_dev: the envelope in the canonical dump layout of LPIC_DIAG_A ((nx+1) x (nr+1)
+ * complex FP64 (re, im) pairs, radial index fastest), in device memory the caller owns.
+ * out_dev: 2 doubles of caller-owned device memory.  Asynchronous on cuda_stream.
+ * It allocates nothing: its scratch (one partial per 4096 nodes) is a fixed 96 KiB array in
+ * the library's device memory, present on every device that loads the library until the
+ * process exits, which limits the input to (nx+1)(nr+1) <= 16,777,216 nodes (LPIC_EBUFSIZE
+ * beyond).  The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Every call rewrites
+ * the partials it uses, so nothing carries over, but all calls share the one array: calls
+ * that overlap on the GPU (on different streams, or from several threads) race.
+ * Returns LPIC_OK, LPIC_EINVAL (NULL pointer, sizes < 1, dr <= 0), LPIC_EBUFSIZE or
+ * LPIC_ECUDA. */
+lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t nr, double dr,
+                                        double *out_dev, void *cuda_stream);
+
 /* Release the context (host memory only; the device buffer stays the caller's). */
 lpic_status lpic_destroy(lpic_ctx *ctx);
 

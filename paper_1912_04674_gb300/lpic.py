@@ -73,6 +73,7 @@ _SIGS = {
     "lpic_set_kernel_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lpic_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "lpic_kernel_name": (C.c_char_p, [C.c_int]),
+    "lpic_envelope_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
     "lpic_destroy": (C.c_int, [C.c_void_p]),
     "lpic_last_error": (C.c_char_p, [C.c_void_p]),
     "lpic_batch_required_bytes": (C.c_size_t, [C.c_int]),
@@ -175,6 +176,15 @@ def lpic_kernel_stats(ctx) -> dict:
 def lpic_kernel_name(k: int) -> str | None:
     v = lib().lpic_kernel_name(int(k))
     return v.decode() if v else None
+
+
+def lpic_envelope_stats_noalloc(a_dev_ptr: int, nx: int, nr: int, dr: float, out_dev_ptr: int,
+                                stream_ptr: int):
+    """Peak |A| and waist from a caller-owned device envelope, without any allocation."""
+    st = lib().lpic_envelope_stats_noalloc(C.c_void_p(a_dev_ptr), int(nx), int(nr), float(dr),
+                                           C.c_void_p(out_dev_ptr), C.c_void_p(stream_ptr))
+    if st != LPIC_OK:
+        raise LpicError(st, "lpic_envelope_stats_noalloc failed")
 
 
 def lpic_destroy(ctx):
