@@ -282,7 +282,10 @@ def run_ours(args):
 
     pk = peaks()
     result = {}
-    for prec, k in (("fp32", args.steps), ("fp64", max(3, args.steps // 8))):
+    plan = [("fp32", args.steps), ("fp64", max(3, args.steps // 8))]
+    if args.precision != "both":
+        plan = [p for p in plan if p[0] == args.precision]
+    for prec, k in plan:
         sim = make_sim(prec)
         sim.step(args.warmup)
         launches0 = sum(v[0] for v in sim.kernel_stats().values())
@@ -302,10 +305,13 @@ def run_ours(args):
         del sim
         torch.cuda.empty_cache()
 
-    acc = accuracy(args.warmup + result["fp64"]["steps"]) if rank == 0 else None
-    e2e = e2e_run("fp32", args.steps) if rank == 0 else None
-    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
-    if rank == 0:
+    extras = rank == 0 and not args.skip_extras and args.precision == "both"
+    acc = accuracy(args.warmup + result["fp64"]["steps"]) if extras else None
+    e2e = e2e_run("fp32", args.steps) if extras else None
+    cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
+    if rank == 0 and args.precision != "both":
+        print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
+    elif rank == 0:
         r32, r64 = result["fp32"], result["fp64"]
         w = WORKLOAD
         line = {
@@ -376,6 +382,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--precision", choices=("both", "fp32", "fp64"), default="both",
+                    help="time one path only (a profiling run, not a bench line)")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the accuracy, end-to-end and CPU legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

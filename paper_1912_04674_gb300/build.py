@@ -19,6 +19,9 @@ LIB = os.path.join(OUT, "liblpic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# The particle kernels' FP32 instantiations use fast single-precision division and square
+# root with subnormals flushed (these flags do not touch FP64 arithmetic).
+PER_FILE = {"particles.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc() -> str:
@@ -49,7 +52,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        per_file = PER_FILE.get(os.path.basename(src), [])
+        cmd = [nvcc, *ARCH, *FLAGS, *per_file, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -30,6 +30,10 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
     if (!g) { msgf(msg, cap, "grid params are NULL"); return LPIC_EINVAL; }
     if (g->nx < 2 || g->nr < 2) { msgf(msg, cap, "nx=%g and nr=%g must be >= 2", g->nx, g->nr); return LPIC_EINVAL; }
     if (g->nr > 65536) { msgf(msg, cap, "nr=%g exceeds 65536", g->nr); return LPIC_EINVAL; }
+    if ((long long)(g->nr + 6) * 2 * (g->nx + 1 + 2 * kG) * 4 >= (1LL << 31)) {
+        msgf(msg, cap, "grid of nx=%g, nr=%g too large for 32-bit element indices", g->nx, g->nr);
+        return LPIC_EINVAL;
+    }
     if ((long long)g->nx * g->nr + 1 > (long long)4096 * 4096) {
         msgf(msg, cap, "nx*nr=%g cells exceeds the counting-sort limit 16777215", (double)g->nx * g->nr);
         return LPIC_EINVAL;
@@ -81,7 +85,7 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
 }
 
 struct Layout {
-    size_t desc, grid[14], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
+    size_t desc, tab, grid[14], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
     int P, nlive, ncol;
 };
 
@@ -95,8 +99,11 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
     L.desc = take(sizeof(Desc));
-    // ex er bt btn phi gx gr phih (R), a0 a1 (2R), chi jx jr dq (double)
-    for (int k = 0; k < 8; k++) L.grid[k] = take(cells * rs);
+    L.tab = take((size_t)NTAB * L.P * rs);
+    // ex er bt btn phih (R), pg (4R), [unused 6, 7], a0 a1 (2R), chi jx jr dq (double)
+    for (int k = 0; k < 5; k++) L.grid[k] = take(cells * rs);
+    L.grid[5] = take(cells * 4 * rs);
+    L.grid[6] = L.grid[7] = 0;
     for (int k = 8; k < 10; k++) L.grid[k] = take(cells * 2 * rs);
     for (int k = 10; k < 14; k++) L.grid[k] = take(cells * 8);
     const size_t cap = (size_t)g->particle_capacity;
@@ -123,8 +130,54 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
 int valid_a_count(const Phys &ph, long long c) {
     int nv = 0;
     for (int a = 0; a < ph.ppcx; a++)
-        if (plasma_density(ph, ((double)c + (a + 0.5) / ph.ppcx) * ph.dx) > 0.0) nv++;
+        if (plasma_density(ph, lattice_x(ph, c, a)) > 0.0) nv++;
     return nv;
+}
+
+// Host-side constants and per-row tables of one simulation.
+template <class R> Kc<R> make_consts(const Phys &ph, const R *tab_dev) {
+    Kc<R> k{};
+    const double dx = ph.dx, dr = ph.dr, dt = ph.dt;
+    k.dt = (R)dt;
+    k.hdt = (R)(0.5 * dt);
+    k.idx = (R)(1.0 / dx);
+    k.idr = (R)(1.0 / dr);
+    k.dtdx = (R)(dt / dx);
+    k.hidx = (R)(0.5 / dx);
+    k.hidr = (R)(0.5 / dr);
+    k.idx2 = (R)(1.0 / (dx * dx));
+    k.idr2 = (R)(1.0 / (dr * dr));
+    k.dt2 = (R)(dt * dt);
+    k.envp = (R)(1.0 / (1.0 + dt * dt));
+    k.envpt = (R)(dt / (1.0 + dt * dt));
+    k.d_dt = dt;
+    k.d_dt2 = dt * dt;
+    k.d_idx2 = 1.0 / (dx * dx);
+    k.d_idr2 = 1.0 / (dr * dr);
+    k.d_hidx = 0.5 / dx;
+    k.d_envp = 1.0 / (1.0 + dt * dt);
+    k.d_envpt = dt / (1.0 + dt * dt);
+    k.d_4idr = 4.0 / dr;
+    k.tab = tab_dev;
+    return k;
+}
+
+std::vector<double> row_tables(const Phys &ph, int P) {
+    std::vector<double> t((size_t)NTAB * P, 0.0);
+    const double dx = ph.dx, dr = ph.dr, dt = ph.dt;
+    for (int j = 0; j < P; j++) {
+        const double vq = j == 0 ? kPi * 0.25 * dr * dr * dx : 2.0 * kPi * j * dr * dr * dx;
+        const double vchi = j == 0 ? kPi * dr * dr * dx / 3.0 : 2.0 * kPi * j * dr * dr * dx;
+        t[(size_t)T_CHI * P + j] = 1.0 / vchi;
+        t[(size_t)T_JX * P + j] = (1.0 / dt) / (vq / dx);
+        t[(size_t)T_JR * P + j] = (1.0 / dt) / (2.0 * kPi * (j + 0.5) * dr * dx);
+        if (j > 0) {
+            t[(size_t)T_ENV1R * P + j] = 1.0 / (2.0 * dr * (j * dr));
+            t[(size_t)T_AMPP * P + j] = ((j + 0.5) * dr) / ((j * dr) * dr);
+            t[(size_t)T_AMPM * P + j] = ((j - 0.5) * dr) / ((j * dr) * dr);
+        }
+    }
+    return t;
 }
 
 }  // namespace
@@ -156,7 +209,7 @@ struct lpic_ctx {
     std::string err;
     bool envelope_set = false;
     // tracing
-    static constexpr int kFamilies = 9;
+    static constexpr int kFamilies = 8;
     long long launches[kFamilies] = {};
     double ms[kFamilies] = {};
     bool timing = false;
@@ -181,8 +234,8 @@ struct lpic_ctx {
 namespace {
 
 const char *const kFamilyNames[lpic_ctx::kFamilies] = {
-    "prepass", "pass_a", "envelope", "pass_b", "ampere", "window", "advance", "sort", "relocate"};
-enum Fam { F_PREPASS, F_PASS_A, F_ENVELOPE, F_PASS_B, F_AMPERE, F_WINDOW, F_ADVANCE, F_SORT, F_RELOCATE };
+    "prepass", "pass_a", "envelope", "pass_b", "ampere", "window", "sort", "relocate"};
+enum Fam { F_PREPASS, F_PASS_A, F_ENVELOPE, F_PASS_B, F_AMPERE, F_WINDOW, F_SORT, F_RELOCATE };
 constexpr int kSortLaunches = 6;  // memset-free launches of one counting sort
 
 cudaEvent_t pool_event(lpic_ctx *c) {
@@ -213,15 +266,14 @@ template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
     const Layout &L = c->L;
     S.geo = c->geo;
     S.ph = c->ph;
+    S.k = make_consts<R>(c->ph, (const R *)(c->buf + c->L.tab));
     S.d = c->d_desc;
     S.f.ex = (R *)(b + L.grid[0]);
     S.f.er = (R *)(b + L.grid[1]);
     S.f.bt = (R *)(b + L.grid[2]);
     S.f.btn = (R *)(b + L.grid[3]);
-    S.f.phi = (R *)(b + L.grid[4]);
-    S.f.gx = (R *)(b + L.grid[5]);
-    S.f.gr = (R *)(b + L.grid[6]);
-    S.f.phih = (R *)(b + L.grid[7]);
+    S.f.phih = (R *)(b + L.grid[4]);
+    S.f.pg = (Q4<R> *)(b + L.grid[5]);
     S.f.a[0] = (typename Cplx<R>::t *)(b + L.grid[8]);
     S.f.a[1] = (typename Cplx<R>::t *)(b + L.grid[9]);
     S.f.chi = (double *)(b + L.grid[10]);
@@ -293,7 +345,6 @@ void enqueue_step_kernels(lpic_ctx *c, const S_ &S, int npl, int inj, cudaStream
     if (npl > 0) traced(c, F_PASS_B, 1, st, [&] { launch_pass_b(S, npl, st); });
     traced(c, F_AMPERE, 1, st, [&] { launch_ampere(S, st); });
     traced(c, F_WINDOW, 1, st, [&] { launch_window(S, inj, st); });
-    traced(c, F_ADVANCE, 1, st, [&] { launch_advance(S, st); });
 }
 
 int inj_upper(const lpic_ctx *c) {
@@ -396,9 +447,15 @@ lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_preci
     c->stage_bytes = L.total - L.stage;
     fill_views(c, c->sd);
     fill_views(c, c->sf);
+    std::vector<double> tab = row_tables(c->ph, L.P);
+    std::vector<float> tabf(tab.begin(), tab.end());
     cudaError_t e = cudaMallocHost((void **)&c->h_desc, sizeof(Desc));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, L.total, c->st);
+    if (e == cudaSuccess)
+        e = prec == LPIC_FP64
+                ? cudaMemcpyAsync(c->buf + L.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->st)
+                : cudaMemcpyAsync(c->buf + L.tab, tabf.data(), tabf.size() * 4, cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) {
         g_thread_err = std::string("lpic_init_grid: ") + cudaGetErrorString(e);
         if (c->h_desc) cudaFreeHost(c->h_desc);
@@ -444,6 +501,11 @@ lpic_status lpic_load_plasma(lpic_ctx *c, const lpic_plasma_params *p) {
     ph.ppcr = p->ppc_r;
     ph.ppct = p->ppc_theta;
     ph.seed = p->seed;
+    ph.inv_ramp = p->ramp_len > 0 ? 1.0 / p->ramp_len : 0.0;
+    ph.inv_ppcx = 1.0 / p->ppc_x;
+    ph.inv_ppcr = 1.0 / p->ppc_r;
+    ph.inv_ppct = 1.0 / p->ppc_theta;
+    ph.wfac = 2.0 * kPi * c->ph.dr * c->ph.dx / ((double)p->ppc_x * p->ppc_r * p->ppc_theta);
     std::vector<int> colbase(c->geo.nx + 1, 0);
     long long total = 0;
     for (int i = 0; i < c->geo.nx; i++) {

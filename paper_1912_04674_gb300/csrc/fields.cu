@@ -26,7 +26,7 @@ template <class R> __global__ void k_prepass(SimDev<R> S) {
     const int i = (int)(blockIdx.y * BY + threadIdx.y) - kG;
     if (j >= g.P || i > g.nx + kG) return;
     const long long id = g.at(off, i, j);
-    const R dt = (R)S.ph.dt, idx_ = (R)(1.0 / S.ph.dx), idr = (R)(1.0 / S.ph.dr);
+    const R dt = S.k.dt, idx_ = S.k.idx, idr = S.k.idr;
 
     if (i >= 0 && i < g.nx && j < g.nr) {
         R bold = S.f.bt[id];
@@ -39,30 +39,26 @@ template <class R> __global__ void k_prepass(SimDev<R> S) {
         S.f.btn[id] = (R)0;
     }
 
+    Q4<R> q4;
+    q4.phi = q4.gx = q4.gr = q4.pad = (R)0;
     if (i >= 0 && i <= g.nx && j <= g.nr) {
         const auto *A = S.f.a[S.d->abuf];
         auto c = A[id];
         auto xp = A[g.at(off, i + 1, j)];   // guard columns of A are zero
         auto xm = A[g.at(off, i - 1, j)];
-        R phc = (R)0.5 * (c.x * c.x + c.y * c.y);
-        R phxp = (R)0.5 * (xp.x * xp.x + xp.y * xp.y);
-        R phxm = (R)0.5 * (xm.x * xm.x + xm.y * xm.y);
-        S.f.phi[id] = phc;
-        S.f.gx[id] = (phxp - phxm) * ((R)0.5 * idx_);
-        if (j == 0) {
-            S.f.gr[id] = (R)0;
-        } else {
+        const R phxp = (R)0.5 * (xp.x * xp.x + xp.y * xp.y);
+        const R phxm = (R)0.5 * (xm.x * xm.x + xm.y * xm.y);
+        q4.phi = (R)0.5 * (c.x * c.x + c.y * c.y);
+        q4.gx = (phxp - phxm) * S.k.hidx;
+        if (j > 0) {
             auto rp = A[id + 1];             // row nr+1 is a zero guard
             auto rm = A[id - 1];
-            R phrp = (R)0.5 * (rp.x * rp.x + rp.y * rp.y);
-            R phrm = (R)0.5 * (rm.x * rm.x + rm.y * rm.y);
-            S.f.gr[id] = (phrp - phrm) * ((R)0.5 * idr);
+            const R phrp = (R)0.5 * (rp.x * rp.x + rp.y * rp.y);
+            const R phrm = (R)0.5 * (rm.x * rm.x + rm.y * rm.y);
+            q4.gr = (phrp - phrm) * S.k.hidr;
         }
-    } else {
-        S.f.phi[id] = (R)0;
-        S.f.gx[id] = (R)0;
-        S.f.gr[id] = (R)0;
     }
+    S.f.pg[id] = q4;
     S.f.chi[id] = 0.0;
     S.f.jx[id] = 0.0;
     S.f.jr[id] = 0.0;
@@ -71,34 +67,31 @@ template <class R> __global__ void k_prepass(SimDev<R> S) {
 
 // One node of Eq. (envelope_solver) in compute precision C:
 //   A^{n+1} = (1+i dt)/(1+dt^2) [2A^n - (1+i dt)A^{n-1} + dt^2 (lap A - chi A + 2i dA/dx)].
+// inv2rj = 1/(2 dr r_j) (unused on the axis row, whose radial part is 4 (A_1 - A_0)/dr^2).
 template <class C, class V>
 __device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V rmin, V amin,
-                                              double chi_d, int j, double dx, double dr,
-                                              double dt, C &ore, C &oim) {
+                                              double chi_d, bool axis, C idx2, C idr2, C inv2rj,
+                                              C hidx, C t, C t2, C p, C pt, C &ore, C &oim) {
     const C cx = (C)cin.x, cy = (C)cin.y;
     const C xpx = (C)xpin.x, xpy = (C)xpin.y, xmx = (C)xmin.x, xmy = (C)xmin.y;
-    const C idx2 = (C)(1.0 / (dx * dx)), idr2 = (C)(1.0 / (dr * dr));
     C lx = (xpx - (C)2 * cx + xmx) * idx2;
     C ly = (xpy - (C)2 * cy + xmy) * idx2;
-    if (j == 0) {
+    if (axis) {
         lx += (C)4 * ((C)rpin.x - cx) * idr2;
         ly += (C)4 * ((C)rpin.y - cy) * idr2;
     } else {
         const C rpx = (C)rpin.x, rpy = (C)rpin.y, rmx = (C)rmin.x, rmy = (C)rmin.y;
-        const C inv2rj = (C)(1.0 / (2.0 * dr * (j * dr)));
         lx += (rpx - (C)2 * cx + rmx) * idr2 + (rpx - rmx) * inv2rj;
         ly += (rpy - (C)2 * cy + rmy) * idr2 + (rpy - rmy) * inv2rj;
     }
-    const C h = (C)(0.5 / dx);
-    const C dxr = (xpx - xmx) * h, dxi = (xpy - xmy) * h;
-    const C chi = (C)chi_d, t = (C)dt, t2 = (C)(dt * dt);
+    const C dxr = (xpx - xmx) * hidx, dxi = (xpy - xmy) * hidx;
+    const C chi = (C)chi_d;
     const C amx = (C)amin.x, amy = (C)amin.y;
     // bracket: lap - chi A + 2i dA/dx
     const C bx = lx - chi * cx - (C)2 * dxi;
     const C by = ly - chi * cy + (C)2 * dxr;
     const C rx = (C)2 * cx - (amx - t * amy) + t2 * bx;
     const C ry = (C)2 * cy - (amy + t * amx) + t2 * by;
-    const C p = (C)(1.0 / (1.0 + dt * dt)), pt = (C)(dt / (1.0 + dt * dt));
     ore = p * rx - pt * ry;
     oim = p * ry + pt * rx;
 }
@@ -123,13 +116,16 @@ template <class R> __global__ void k_envelope(SimDev<R> S) {
     auto am = Am[id];
     const double chi = S.f.chi[id];
     R nre, nim;
+    const Kc<R> &K = S.k;
     if (j == 0) {  // axis row in FP64
         double dre, dim;
-        envelope_node<double>(c, xp, xm, rp, rm, am, chi, 0, S.ph.dx, S.ph.dr, S.ph.dt, dre, dim);
+        envelope_node<double>(c, xp, xm, rp, rm, am, chi, true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
+                              K.d_dt, K.d_dt2, K.d_envp, K.d_envpt, dre, dim);
         nre = (R)dre;
         nim = (R)dim;
     } else {
-        envelope_node<R>(c, xp, xm, rp, rm, am, chi, j, S.ph.dx, S.ph.dr, S.ph.dt, nre, nim);
+        envelope_node<R>(c, xp, xm, rp, rm, am, chi, false, K.idx2, K.idr2, K.tab[T_ENV1R * g.P + j],
+                         K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
     }
     typename Cplx<R>::t o;
     o.x = nre;
@@ -147,25 +143,24 @@ template <class R> __global__ void k_ampere(SimDev<R> S) {
     const int i = blockIdx.y * BY + threadIdx.y;
     if (j > g.nr || i > g.nx) return;
     const long long id = g.at(off, i, j);
-    const double dt = S.ph.dt, dx = S.ph.dx, dr = S.ph.dr;
+    const R dt = S.k.dt;
     if (j < g.nr) {
         if (i == 0 || i == g.nx) {
             S.f.er[id] = (R)0;
         } else {
-            R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * (R)(1.0 / dx);
-            S.f.er[id] += (R)dt * (-dbdx - (R)S.f.jr[id]);
+            R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * S.k.idx;
+            S.f.er[id] += dt * (-dbdx - (R)S.f.jr[id]);
         }
     }
     if (i < g.nx) {
         if (j == g.nr) {
             S.f.ex[id] = (R)0;
         } else if (j == 0) {  // axis row in FP64
-            double curl = 4.0 * (double)S.f.bt[id] / dr;
-            S.f.ex[id] = (R)((double)S.f.ex[id] + dt * (curl - S.f.jx[id]));
+            double curl = S.k.d_4idr * (double)S.f.bt[id];
+            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jx[id]));
         } else {
-            R rp = (R)((j + 0.5) * dr), rm = (R)((j - 0.5) * dr);
-            R curl = (rp * S.f.bt[id] - rm * S.f.bt[id - 1]) * (R)(1.0 / ((j * dr) * dr));
-            S.f.ex[id] += (R)dt * (curl - (R)S.f.jx[id]);
+            R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
+            S.f.ex[id] += dt * (curl - (R)S.f.jx[id]);
         }
     }
 }

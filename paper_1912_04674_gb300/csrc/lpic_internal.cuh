@@ -34,7 +34,8 @@ struct Desc {
     int pbuf;          // index of the particle buffer in use (the other is the sort target)
     int last_shift;    // 1 if the last step ended with a window shift (its deposits sit one
                        // physical column before the current window)
-    int pad[5];
+    unsigned done;     // blocks of the window kernel finished this step (last one advances)
+    int pad[4];
 };
 static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
 
@@ -47,15 +48,22 @@ struct Geo {
     int P;        // column stride in elements
     int ncol;     // physical columns of every grid array
     int nlive;    // nx + 1 + 2*kG columns of the live window (incl. guards)
-    __host__ __device__ __forceinline__ long long at(int off, int i, int j) const {
-        return (long long)(off + kG + i) * P + j;
+    // element index; every grid array has fewer than 2^31 elements (checked at set-up)
+    __host__ __device__ __forceinline__ int at(int off, int i, int j) const {
+        return (off + kG + i) * P + j;
     }
+};
+
+// Phi^n and its two centred differences at one node, loaded together by the gathers.
+template <class R> struct alignas(4 * sizeof(R)) Q4 {
+    R phi, gx, gr, pad;
 };
 
 template <class R> struct Fields {
     R *ex, *er, *bt;                 // persistent: E^n, B^{n-1/2} -> B^{n+1/2}
     typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
-    R *btn, *phi, *gx, *gr, *phih;   // per step: B^n, Phi^n, dPhi/dx, dPhi/dr, Phi^{n+1/2}
+    R *btn, *phih;                   // per step: B^n, Phi^{n+1/2}
+    Q4<R> *pg;                       // per step: (Phi^n, dPhi/dx, dPhi/dr)
     double *chi, *jx, *jr, *dq;      // per step FP64 accumulators
 };
 
@@ -74,11 +82,33 @@ struct Phys {
     unsigned long long seed;
     int cap;
     int track_dq;
+    // host-computed reciprocals for the lattice generator
+    double inv_ramp, inv_ppcx, inv_ppcr, inv_ppct, wfac;  // wfac = 2 pi dr dx / ppc
+};
+
+// Per-row tables (device, P entries each, working precision), filled once at set-up.
+enum RowTab : int {
+    T_CHI = 0,   // 1 / V_chi(j)
+    T_JX,        // (1/dt) / (V_j / dx): current from a charge flux through an x face
+    T_JR,        // (1/dt) / (2 pi r_{j+1/2} dx): through an r face
+    T_ENV1R,     // 1 / (2 dr r_j), j >= 1 (envelope radial term)
+    T_AMPP,      // r_{j+1/2} / (r_j dr), j >= 1 (Ampere)
+    T_AMPM,      // r_{j-1/2} / (r_j dr), j >= 1
+    NTAB
+};
+
+// Constants of one simulation, computed on the host (FP64 is a slow pipe on this part,
+// so no kernel derives them per thread).
+template <class R> struct Kc {
+    R dt, hdt, idx, idr, dtdx, hidx, hidr, idx2, idr2, dt2, envp, envpt;
+    double d_dt, d_dt2, d_idx2, d_idr2, d_hidx, d_envp, d_envpt, d_4idr;  // FP64 axis rows
+    const R *tab;   // NTAB x P row tables
 };
 
 template <class R> struct SimDev {
     Geo geo;
     Phys ph;
+    Kc<R> k;
     Desc *d;
     Fields<R> f;
     Parts<R> p[2];   // p[d->pbuf] in use; the counting sort scatters into the other
@@ -88,8 +118,13 @@ template <class R> struct SimDev {
 __host__ __device__ __forceinline__ double plasma_density(const Phys &ph, double xlab) {
     if (xlab < ph.x_start) return 0.0;
     if (ph.ramp_len > 0.0 && xlab < ph.x_start + ph.ramp_len)
-        return ph.n0 * (xlab - ph.x_start) / ph.ramp_len;
+        return ph.n0 * (xlab - ph.x_start) * ph.inv_ramp;
     return ph.n0;
+}
+
+// lab x of lattice slice a of lab column c
+__host__ __device__ __forceinline__ double lattice_x(const Phys &ph, long long c, int a) {
+    return ((double)c + (a + 0.5) * ph.inv_ppcx) * ph.dx;
 }
 
 // k-th output of SplitMix64 seeded with `seed` (Steele, Lea, Flood 2014).
@@ -116,10 +151,8 @@ __device__ __forceinline__ bool lattice_particle(const SimDev<R> &S, long long c
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     int valid[16];
     int nv = 0;
-    for (int a = 0; a < ph.ppcx && a < 16; a++) {
-        double xl = ((double)c + (a + 0.5) / ph.ppcx) * ph.dx;
-        if (plasma_density(ph, xl) > 0.0) valid[nv++] = a;
-    }
+    for (int a = 0; a < ph.ppcx && a < 16; a++)
+        if (plasma_density(ph, lattice_x(ph, c, a)) > 0.0) valid[nv++] = a;
     const int perj = nv * ph.ppcr * ph.ppct;
     if (perj == 0 || local >= perj * S.geo.nr) return false;
     const int j = local / perj;
@@ -128,22 +161,30 @@ __device__ __forceinline__ bool lattice_particle(const SimDev<R> &S, long long c
     rem -= av * ph.ppcr * ph.ppct;
     const int b = rem / ph.ppct, kk = rem - b * ph.ppct;
     const int a = valid[av];
-    const double xl = ((double)c + (a + 0.5) / ph.ppcx) * ph.dx;
-    const double n = plasma_density(ph, xl);
-    const double r = (j + (b + 0.5) / ph.ppcr) * ph.dr;
+    const double n = plasma_density(ph, lattice_x(ph, c, a));
+    const double r = (j + (b + 0.5) * ph.inv_ppcr) * ph.dr;
     const unsigned long long cell = (unsigned long long)c * S.geo.nr + (unsigned long long)j;
     const double u = (double)(splitmix64(ph.seed, cell + 1) >> 11) * (1.0 / 9007199254740992.0);
-    const double th = 2.0 * kPi * (kk + u) / ph.ppct;
-    double sn, cs;
-    sincos(th, &sn, &cs);
+    R sn, cs;
+    if (sizeof(R) == 4) {   // FP32 positions: the angle in FP32 is as exact as they are
+        float sf, cf;
+        sincosf((float)(2.0 * kPi * ((kk + u) * ph.inv_ppct)), &sf, &cf);
+        sn = (R)sf;
+        cs = (R)cf;
+    } else {
+        double sd, cd;
+        sincos(2.0 * kPi * ((kk + u) * ph.inv_ppct), &sd, &cd);
+        sn = (R)sd;
+        cs = (R)cd;
+    }
     P.ix[slot] = (int)c;
-    P.ox[slot] = (R)((a + 0.5) / ph.ppcx);
-    P.y[slot] = (R)(r * cs);
-    P.z[slot] = (R)(r * sn);
+    P.ox[slot] = (R)((a + 0.5) * ph.inv_ppcx);
+    P.y[slot] = (R)r * cs;
+    P.z[slot] = (R)r * sn;
     P.px[slot] = (R)0;
     P.py[slot] = (R)0;
     P.pz[slot] = (R)0;
-    P.w[slot] = (R)(n * 2.0 * kPi * r * ph.dr * ph.dx / (ph.ppcx * ph.ppcr * ph.ppct));
+    P.w[slot] = (R)(n * r * ph.wfac);
     P.id[slot] = ((cell * ph.ppcx + a) * ph.ppcr + b) * ph.ppct + kk;
     return true;
 }
@@ -155,7 +196,6 @@ template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st);
 template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st);
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st);
 template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st);
-template <class R> void launch_advance(const SimDev<R> &S, cudaStream_t st);
 
 template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
                                             double xc, double xf, cudaStream_t st);

@@ -2,9 +2,13 @@
 // momentum push), pass B (time-centred position push, charge-conserving current deposit,
 // removal at the window edges) and the lattice loader.
 //
-// One thread per particle slot, grid-stride over the slot count held on the device.
-// Particles are kept counting-sorted by cell, so the threads of a warp gather from a few
-// neighbouring columns (L1 hits) and the FP64 atomics of a warp land on a few lines.
+// Work is split into warp-sized groups of consecutive particle slots (a warp-uniform loop,
+// so that every lane takes part in the warp-level reductions).  Particles are kept
+// counting-sorted by cell, so runs of neighbouring lanes deposit onto the same nodes: each
+// deposit is first summed over its run with a segmented shuffle reduction (compensated
+// TwoSum in FP32), and only the run's first lane issues the FP64 global atomic.
+#include <mutex>
+
 #include "lpic_internal.cuh"
 
 namespace lpic {
@@ -12,6 +16,8 @@ namespace lpic {
 namespace {
 
 constexpr int TPB = 256;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned kNoKey = 0xffffffffu;
 
 // Linear-weight position of a particle on the four grids a gather can use.
 template <class R> struct Loc {
@@ -38,24 +44,155 @@ __device__ __forceinline__ Loc<R> locate(int irel, R ox, R rn, int nx, int nr) {
 }
 
 // Gather with weights (1-f)(1-g), f(1-g), (1-f)g, fg; for odd-in-r quantities the ghost row
-// j = -1 reads -F(j = 0).
+// j = -1 reads -F(j = 0) (selects, no branch).
 template <class R>
 __device__ __forceinline__ R gather4(const R *__restrict__ F, const Geo &geo, int off, int i,
                                      R f, int j, R gw, bool odd_ghost) {
-    const long long b = geo.at(off, i, j < 0 ? 0 : j);
-    R f00 = __ldg(F + b), f10 = __ldg(F + b + geo.P);
-    R f01, f11;
-    if (j < 0 && odd_ghost) {
-        f01 = f00; f11 = f10; f00 = -f00; f10 = -f10;
-    } else {
-        f01 = __ldg(F + b + 1); f11 = __ldg(F + b + geo.P + 1);
-    }
+    const bool ghost = odd_ghost && j < 0;
+    const int b = geo.at(off, i, j < 0 ? 0 : j);
+    const int up = ghost ? 0 : 1;
+    const R l0 = __ldg(F + b), l1 = __ldg(F + b + geo.P);
+    const R f01 = __ldg(F + b + up), f11 = __ldg(F + b + geo.P + up);
+    const R f00 = ghost ? -l0 : l0, f10 = ghost ? -l1 : l1;
     return ((R)1 - f) * ((R)1 - gw) * f00 + f * ((R)1 - gw) * f10 + ((R)1 - f) * gw * f01 +
            f * gw * f11;
 }
 
-__device__ __forceinline__ void red_add(double *p, double v) {
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+
+// FP32 -> FP64 from the IEEE-754 field layouts with integer operations (the FP64 pipe is
+// slow on this part): exponent rebiased by 1023 - 127 = 896, mantissa widened.  FP32
+// subnormals (< 1.2e-38) become 0; infinities and NaNs stay what they are.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x), sgn = u & 0x80000000u, m = u & 0x7fffffffu;
+    const bool tiny = m < 0x00800000u, special = m >= 0x7f800000u;
+    const unsigned hi_n = sgn | ((m >> 3) + (896u << 20));
+    const unsigned hi_s = sgn | 0x7ff00000u | ((m & 0x007fffffu) >> 3);
+    const unsigned hi = tiny ? sgn : (special ? hi_s : hi_n);
+    const unsigned lo = tiny ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ void atom_add(double *p, double v) {
     if (v != 0.0) atomicAdd(p, v);
+}
+__device__ __forceinline__ void atom_add(double *p, float v) {
+    if (v != 0.0f) atomicAdd(p, f2d_bits(v));
+}
+
+// Sum of each deposit over the lanes of a warp that share its key (same target node);
+// returns true on one lane per key (the lowest), which then holds the sums.
+//  FP64: segmented shuffle sums over runs of consecutive lanes.
+//  FP32: exact integer accumulation -- each value is scaled by a power of two set by the
+//  largest exponent of its group (so that 32 of them cannot overflow 31 bits), rounded to an
+//  integer, summed exactly with one warp reduction, and scaled back: the group sum carries a
+//  single rounding of 2^-24 of the group's largest value.
+template <int N> __device__ __forceinline__ bool run_sum(unsigned key, double (&v)[N]) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int run = __popc(heads & (0xffffffffu >> (31u - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int orun = __shfl_down_sync(FULL, run, o);
+        const bool ok = lane + o < 32u && orun == run;
+#pragma unroll
+        for (int q = 0; q < N; q++) {
+            const double ov = __shfl_down_sync(FULL, v[q], o);
+            if (ok) v[q] += ov;
+        }
+    }
+    return head;
+}
+
+template <int N> __device__ __forceinline__ bool run_sum(unsigned key, float (&v)[N]) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const bool head = (unsigned)(__ffs(grp) - 1) == lane;
+#pragma unroll
+    for (int q = 0; q < N; q++) {
+        const unsigned e = ((unsigned)__float_as_int(v[q]) >> 23) & 0xffu;
+        const int emax = (int)__reduce_max_sync(grp, e);   // |v| < 2^(emax - 126)
+        const int ec = min(max(emax, 25), 254);
+        const float sc = __int_as_float((278 - ec) << 23);    // 2^(151 - emax)
+        const float isc = __int_as_float((ec - 24) << 23);    // 2^(emax - 151)
+        const int s = __reduce_add_sync(grp, __float2int_rn(v[q] * sc));   // |.| < 2^30
+        // groups below 2^-101 are dropped; a non-finite value makes the sum NaN
+        v[q] = emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)s * isc);
+    }
+    return head;
+}
+
+// As run_sum, for deposits whose magnitudes are bounded by per-lane values bnd[]: values
+// q < N/M share bound 0, the next N/M bound 1, ... (one exponent reduction per bound).
+template <int N, int M>
+__device__ __forceinline__ bool run_sum_bounded(unsigned key, float (&v)[N], const float (&bnd)[M]) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const bool head = (unsigned)(__ffs(grp) - 1) == lane;
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        const unsigned e = ((unsigned)__float_as_int(bnd[m]) >> 23) & 0xffu;
+        const int emax = (int)__reduce_max_sync(grp, e);   // every |v| of this bound < 2^(emax - 126)
+        const int ec = min(max(emax, 25), 254);
+        const float sc = __int_as_float((278 - ec) << 23);
+        const float isc = __int_as_float((ec - 24) << 23);
+#pragma unroll
+        for (int q = m * (N / M); q < (m + 1) * (N / M); q++) {
+            const int s = __reduce_add_sync(grp, __float2int_rn(v[q] * sc));
+            v[q] = emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)s * isc);
+        }
+    }
+    return head;
+}
+template <int N, int M>
+__device__ __forceinline__ bool run_sum_bounded(unsigned key, double (&v)[N], const double (&)[M]) {
+    return run_sum<N>(key, v);
+}
+
+// After run_sum(_bounded) the group's sums v[0..3] sit on every lane of the group in FP32
+// (the integer reduction broadcasts), so the group's four atomics are issued by four of its
+// lanes at once.  In FP64 only the head holds them.  addr[q], fac[q]: target and row factor.
+__device__ __forceinline__ void group_atomics(unsigned key, bool head, const float (&v)[4],
+                                              double *const (&addr)[4], const float (&fac)[4]) {
+    if (key == kNoKey) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned grp = __match_any_sync(__activemask(), key);
+    const int gsize = __popc(grp), rank = __popc(grp & ((1u << lane) - 1u));
+    (void)head;
+    for (int q = rank; q < 4; q += gsize) {
+        const float val = q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
+        const float f = q == 0 ? fac[0] : q == 1 ? fac[1] : q == 2 ? fac[2] : fac[3];
+        double *const a = q == 0 ? addr[0] : q == 1 ? addr[1] : q == 2 ? addr[2] : addr[3];
+        atom_add(a, val * f);
+    }
+}
+__device__ __forceinline__ void group_atomics(unsigned key, bool head, const double (&v)[4],
+                                              double *const (&addr)[4], const double (&fac)[4]) {
+    if (!head || key == kNoKey) return;
+#pragma unroll
+    for (int q = 0; q < 4; q++) atom_add(addr[q], v[q] * fac[q]);
+}
+
+// Particle registers of one slot.
+template <class R> struct PReg {
+    int ix;
+    R ox, y, z, px, py, pz, w;
+};
+template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<R> &P, int k, int np) {
+    PReg<R> q;
+    if (k < np) {
+        q.ix = P.ix[k];
+        q.ox = P.ox[k]; q.y = P.y[k]; q.z = P.z[k];
+        q.px = P.px[k]; q.py = P.py[k]; q.pz = P.pz[k]; q.w = P.w[k];
+    } else {
+        q.ix = kDead;
+        q.ox = q.y = q.z = q.px = q.py = q.pz = q.w = (R)0;
+    }
+    return q;
 }
 
 // Pass A (paper Eqs. EquationsOfMotion and motion_equations_cartesian, modified Boris of
@@ -67,77 +204,98 @@ template <class R> __global__ void __launch_bounds__(TPB) k_pass_a(SimDev<R> S) 
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
     const long long shift = S.d->shift;
-    const R dt = (R)S.ph.dt, hdt = (R)(0.5 * S.ph.dt), idr = (R)(1.0 / S.ph.dr);
-    const double cv0 = 3.0 / (kPi * S.ph.dr * S.ph.dr * S.ph.dx);      // 1/V_chi(axis)
-    const double cv1 = 1.0 / (2.0 * kPi * S.ph.dr * S.ph.dr * S.ph.dx); // j/V_chi(j)
+    const R hdt = S.k.hdt, idr = S.k.idr;
+    const R *__restrict__ tchi = S.k.tab + T_CHI * geo.P;
     const R q = (R)-1;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
-        const int ix = P.ix[k];
-        if (ix == kDead) continue;
-        const int irel = (int)((long long)ix - shift);
-        const R ox = P.ox[k], y = P.y[k], z = P.z[k], w = P.w[k];
-        R px = P.px[k], py = P.py[k], pz = P.pz[k];
-        const R r = sqrt(y * y + z * z);
-        R ct = (R)1, st = (R)0;
-        if (r > (R)0) { ct = y / r; st = z / r; }
-        const Loc<R> L = locate<R>(irel, ox, r * idr, geo.nx, geo.nr);
-        const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
-        const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
-        const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
-        const R phg = gather4<R>(S.f.phi, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-        const R gxg = gather4<R>(S.f.gx, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-        const R grg = gather4<R>(S.f.gr, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-        const R Ex = exg, Ey = erg * ct, Ez = erg * st;
-        const R By = -btg * st, Bz = btg * ct;               // Bx = 0
-        const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
+    const int lane = threadIdx.x & 31;
+    const int stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    int k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    PReg<R> cur = load_particle<R>(P, k0 + lane, np);
+    for (; k0 < np; k0 += stride) {
+        const int k = k0 + lane;
+        const PReg<R> nxt = load_particle<R>(P, k + stride, np);   // prefetch
+        R v[4] = {0, 0, 0, 0}, bnd[1] = {0};
+        unsigned key = kNoKey;
+        int b = 0, jp = 0;
+        if (cur.ix != kDead) {
+            const int irel = (int)((long long)cur.ix - shift);
+            const R y = cur.y, z = cur.z, w = cur.w, px = cur.px, py = cur.py, pz = cur.pz;
+            const R r2 = y * y + z * z;
+            R r = (R)0, ct = (R)1, st = (R)0;
+            if (r2 > (R)0) {
+                const R ir = rsqrt_<R>(r2);
+                r = r2 * ir;
+                ct = y * ir;
+                st = z * ir;
+            }
+            const Loc<R> L = locate<R>(irel, cur.ox, r * idr, geo.nx, geo.nr);
+            const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
+            const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
+            const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
+            // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
+            b = geo.at(off, L.ip, L.jp);
+            const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
+            const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
+            const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
+            const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
+            const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
+            const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
+            const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
+            const R Ex = exg, Ey = erg * ct, Ez = erg * st;
+            const R By = -btg * st, Bz = btg * ct;               // Bx = 0
+            const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
 
-        const R g0 = sqrt((R)1 + px * px + py * py + pz * pz + phg);
-        const R i2g0 = (R)0.5 / g0;
-        const R sx = px + hdt * (q * Ex - Gx * i2g0);
-        const R sy = py + hdt * (q * Ey - Gy * i2g0);
-        const R sz = pz + hdt * (q * Ez - Gz * i2g0);
-        const R gt = sqrt((R)1 + sx * sx + sy * sy + sz * sz + phg);
+            const R i2g0 = (R)0.5 * rsqrt_<R>((R)1 + px * px + py * py + pz * pz + phg);
+            const R sx = px + hdt * (q * Ex - Gx * i2g0);
+            const R sy = py + hdt * (q * Ey - Gy * i2g0);
+            const R sz = pz + hdt * (q * Ez - Gz * i2g0);
+            const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
 
-        // susceptibility deposit on the primal nodes
-        {
-            const double base = (double)w / (double)gt;
-            const double wx0 = (double)((R)1 - L.fp), wx1 = (double)L.fp;
-            const double wr0 = (double)((R)1 - L.gp), wr1 = (double)L.gp;
-            const double iv0 = L.jp == 0 ? cv0 : cv1 / L.jp;
-            const double iv1 = cv1 / (L.jp + 1);
-            const long long b = geo.at(off, L.ip, L.jp);
-            red_add(S.f.chi + b, base * wx0 * wr0 * iv0);
-            red_add(S.f.chi + b + geo.P, base * wx1 * wr0 * iv0);
-            red_add(S.f.chi + b + 1, base * wx0 * wr1 * iv1);
-            red_add(S.f.chi + b + geo.P + 1, base * wx1 * wr1 * iv1);
+            // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1); the 1/V factor
+            // is applied per row after the sum over lanes
+            const R base = w * rgt;
+            bnd[0] = base;
+            v[0] = base * w00;
+            v[1] = base * w10;
+            v[2] = base * w01;
+            v[3] = base * w11;
+            jp = L.jp;
+            key = (unsigned)b;
+
+            const R i2gt = (R)0.5 * rgt;
+            const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
+            const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
+            const R tf = q * hdt * rsqrt_<R>((R)1 + mx * mx + my * my + mz * mz + phg);
+            const R ty = tf * By, tz = tf * Bz;                  // tx = 0
+            const R sf = (R)2 / ((R)1 + ty * ty + tz * tz);
+            const R vy = sf * ty, vz = sf * tz;
+            // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
+            const R ppx = mx + (my * tz - mz * ty);
+            const R ppy = my + (-mx * tz);
+            const R ppz = mz + (mx * ty);
+            P.px[k] = mx + (ppy * vz - ppz * vy) + hdt * Fx;
+            P.py[k] = my + (-ppx * vz) + hdt * Fy;
+            P.pz[k] = mz + (ppx * vy) + hdt * Fz;
         }
-
-        const R i2gt = (R)0.5 / gt;
-        const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
-        const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
-        const R gm = sqrt((R)1 + mx * mx + my * my + mz * mz + phg);
-        const R tf = q * hdt / gm;
-        const R ty = tf * By, tz = tf * Bz;                  // tx = 0
-        const R t2 = ty * ty + tz * tz;
-        const R sf = (R)2 / ((R)1 + t2);
-        const R vy = sf * ty, vz = sf * tz;
-        // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
-        const R ppx = mx + (my * tz - mz * ty);
-        const R ppy = my + (-mx * tz);
-        const R ppz = mz + (mx * ty);
-        const R plx = mx + (ppy * vz - ppz * vy);
-        const R ply = my + (-ppx * vz);
-        const R plz = mz + (ppx * vy);
-        P.px[k] = plx + hdt * Fx;
-        P.py[k] = ply + hdt * Fy;
-        P.pz[k] = plz + hdt * Fz;
+        {
+            const bool head = run_sum_bounded<4, 1>(key, v, bnd);
+            const R i0 = tchi[jp], i1 = tchi[jp + 1];
+            double *const addr[4] = {S.f.chi + b, S.f.chi + b + geo.P, S.f.chi + b + 1,
+                                     S.f.chi + b + geo.P + 1};
+            const R fac[4] = {i0, i0, i1, i1};
+            group_atomics(key, head, v, addr, fac);
+        }
+        cur = nxt;
     }
 }
 
+// Linear shape of a particle in cell i0 with fraction f, on the nodes base, base+1, base+2
+// (i0 is base or base+1); written with selects so the arrays stay in registers.
 template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base, R *s) {
-    s[0] = s[1] = s[2] = (R)0;
-    s[i0 - base] = (R)1 - f;
-    s[i0 - base + 1] = f;
+    const bool lo = i0 == base;
+    s[0] = lo ? (R)1 - f : (R)0;
+    s[1] = lo ? f : (R)1 - f;
+    s[2] = lo ? (R)0 : f;
 }
 
 // Pass B: Phi^{n+1/2} at x^n, gbar = sqrt(1+|p|^2+Phi^{n+1/2}), x^{n+1} = x^n + dt p/gbar;
@@ -145,105 +303,137 @@ template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base,
 //   Wx = DSx (S0r + DSr/2), Wr = DSr (S0x + DSx/2),
 //   Jx(i+1/2,j) = (-q w/dt) sum_{k<=i} Wx(k,j) / (V_j/dx),
 //   Jr(i,j+1/2) = (-q w/dt) sum_{l<=j} Wr(i,l) / (2 pi r_{j+1/2} dx).
-// Particles leaving the next step's window (x < 0, x >= Nx dx) or reaching r >= r_max are
-// marked dead after their deposit.
+// A particle that stays in its cell has only four non-zero terms,
+//   Jx(i+1/2, j)   ~ -w dx_ (1 - rbar),  Jx(i+1/2, j+1) ~ -w dx_ rbar,
+//   Jr(i, j+1/2)   ~ -w dr_ (1 - xbar),  Jr(i+1, j+1/2) ~ -w dr_ xbar,
+// (dx_, dr_ the in-cell displacements, xbar, rbar the mean fractions); those are summed over
+// the lanes sharing the cell before the atomics.  Cell-crossing particles take the 3x3
+// general form.  Particles leaving the next step's window (x < 0, x >= Nx dx) or reaching
+// r >= r_max are marked dead after their deposit.
 template <class R> __global__ void __launch_bounds__(TPB) k_pass_b(SimDev<R> S) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
     const long long shift = S.d->shift, step = S.d->step;
     const int snext = window_shifts(S.ph, step, shift) ? 1 : 0;
-    const R dt = (R)S.ph.dt, idr = (R)(1.0 / S.ph.dr), dtdx = (R)(S.ph.dt / S.ph.dx);
-    const double rmax = geo.nr * S.ph.dr;
-    const double ax0 = 1.0 / (kPi * 0.25 * S.ph.dr * S.ph.dr);       // 1/(V_0/dx)
-    const double ax1 = 1.0 / (2.0 * kPi * S.ph.dr * S.ph.dr);        // j/(V_j/dx)
-    const double ar = 1.0 / (2.0 * kPi * S.ph.dr * S.ph.dx);         // (j+1/2)*(1/area_r)
-    const double jfac = 1.0 / S.ph.dt;                               // -q/dt, q = -1
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
-        const int ix = P.ix[k];
-        if (ix == kDead) continue;
-        const int irel = (int)((long long)ix - shift);
-        const R ox = P.ox[k], y = P.y[k], z = P.z[k], w = P.w[k];
-        const R px = P.px[k], py = P.py[k], pz = P.pz[k];
-        const R r0 = sqrt(y * y + z * z);
-        const R rn0 = r0 * idr;
-        const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
-        const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-        const R gbar = sqrt((R)1 + px * px + py * py + pz * pz + ph);
-        const R ig = (R)1 / gbar;
-        // The current is a difference of shape factors at two nearby positions: move x as
-        // an in-cell offset, and take the new radius as r^n plus the radial step in the
-        // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
-        R ox1 = ox + dtdx * px * ig;
-        const R dy = dt * py * ig, dz = dt * pz * ig;
-        const R y1 = y + dy, z1 = z + dz;
-        // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
-        // keep the 3-node shape window in range for non-finite input
-        int di = min(max((int)floor(ox1), -1), 1);
-        ox1 -= (R)di;
-        if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
-        const int ia = L.ip, ib = L.ip + di;
-        const R r1 = sqrt(y1 * y1 + z1 * z1);
-        const R rsum = r0 + r1;
-        const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
-        R rn1 = rn0 + step_r * idr;
-        if (rn1 < (R)0) rn1 = (R)0;
-        const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
-        const R fra = L.gp, frb = rn1 - (R)jb;
-        const int imin = min(ia, ib), jmin = min(ja, jb);
-        R s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
-        shape3<R>(ia, ox, imin, s0x);
-        shape3<R>(ib, ox1, imin, s1x);
-        shape3<R>(ja, fra, jmin, s0r);
-        shape3<R>(jb, frb, jmin, s1r);
+    const R dt = S.k.dt, idr = S.k.idr, dtdx = S.k.dtdx;
+    const R rmax = (R)(geo.nr * S.ph.dr);
+    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
+    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
+    const int lane = threadIdx.x & 31;
+    const int stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    int k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    PReg<R> cur = load_particle<R>(P, k0 + lane, np);
+    for (; k0 < np; k0 += stride) {
+        const int k = k0 + lane;
+        const PReg<R> nxt = load_particle<R>(P, k + stride, np);   // prefetch
+        R v[4] = {0, 0, 0, 0}, bnd[2] = {0, 0};
+        unsigned key = kNoKey;
+        int b = 0, jrow = 0;
+        if (cur.ix != kDead) {
+            const int ix = cur.ix;
+            const int irel = (int)((long long)ix - shift);
+            const R ox = cur.ox, y = cur.y, z = cur.z, w = cur.w;
+            const R px = cur.px, py = cur.py, pz = cur.pz;
+            const R r0 = sqrt(y * y + z * z);
+            const R rn0 = r0 * idr;
+            const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
+            const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
+            const R ig = rsqrt_<R>((R)1 + px * px + py * py + pz * pz + ph);   // 1/gbar
+            // The current is a difference of shape factors at two nearby positions: move x as
+            // an in-cell offset, and take the new radius as r^n plus the radial step in the
+            // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
+            R ox1 = ox + dtdx * px * ig;
+            const R dy = dt * py * ig, dz = dt * pz * ig;
+            const R y1 = y + dy, z1 = z + dz;
+            // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
+            // keep the 3-node shape window in range for non-finite input
+            int di = min(max((int)floor(ox1), -1), 1);
+            ox1 -= (R)di;
+            if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
+            const int ia = L.ip, ib = L.ip + di;
+            const R r1 = sqrt(y1 * y1 + z1 * z1);
+            const R rsum = r0 + r1;
+            const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
+            R rn1 = rn0 + step_r * idr;
+            if (rn1 < (R)0) rn1 = (R)0;
+            const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
+            const R fra = L.gp, frb = rn1 - (R)jb;
+
+            if (ia == ib && ja == jb) {
+                const R ddx = ox1 - ox, ddr = frb - fra;
+                const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
+                bnd[0] = w * ddx;
+                bnd[1] = w * ddr;
+                v[0] = -bnd[0] * ((R)1 - rbar);
+                v[1] = -bnd[0] * rbar;
+                v[2] = -bnd[1] * ((R)1 - xbar);
+                v[3] = -bnd[1] * xbar;
+                b = geo.at(off, ia, ja);
+                jrow = ja;
+                key = (unsigned)b;
+            } else {
+                const int imin = min(ia, ib), jmin = min(ja, jb);
+                R s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
+                shape3<R>(ia, ox, imin, s0x);
+                shape3<R>(ib, ox1, imin, s1x);
+                shape3<R>(ja, fra, jmin, s0r);
+                shape3<R>(jb, frb, jmin, s1r);
 #pragma unroll
-        for (int c = 0; c < 3; c++) { dsx[c] = s1x[c] - s0x[c]; dsr[c] = s1r[c] - s0r[c]; }
-        const double qf = (double)w * jfac;
-        const long long b = geo.at(off, imin, jmin);
+                for (int cc = 0; cc < 3; cc++) { dsx[cc] = s1x[cc] - s0x[cc]; dsr[cc] = s1r[cc] - s0r[cc]; }
+                const int bb = geo.at(off, imin, jmin);
 #pragma unroll
-        for (int l = 0; l < 3; l++) {
-            const int j = jmin + l;
-            const double inva = j == 0 ? ax0 : ax1 / j;
-            R acc = (R)0;
+                for (int l = 0; l < 3; l++) {
+                    R acc = (R)0;
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-                acc += dsx[c] * (s0r[l] + (R)0.5 * dsr[l]);
-                red_add(S.f.jx + b + (long long)c * geo.P + l, qf * (double)acc * inva);
+                    for (int cc = 0; cc < 2; cc++) {
+                        acc += dsx[cc] * (s0r[l] + (R)0.5 * dsr[l]);
+                        atom_add(S.f.jx + bb + cc * geo.P + l, w * acc * tjx[jmin + l]);
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    R acc = (R)0;
+#pragma unroll
+                    for (int l = 0; l < 2; l++) {
+                        acc += dsr[l] * (s0x[cc] + (R)0.5 * dsx[cc]);
+                        atom_add(S.f.jr + bb + cc * geo.P + l, w * acc * tjr[jmin + l]);
+                    }
+                }
             }
-        }
+            if (S.ph.track_dq) {   // diagnostic: charge change q w (S1 - S0), general form
+                const int imin = min(ia, ib), jmin = min(ja, jb);
+                R s0x[3], s1x[3], s0r[3], s1r[3];
+                shape3<R>(ia, ox, imin, s0x);
+                shape3<R>(ib, ox1, imin, s1x);
+                shape3<R>(ja, fra, jmin, s0r);
+                shape3<R>(jb, frb, jmin, s1r);
+                const int bb = geo.at(off, imin, jmin);
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            R acc = (R)0;
+                for (int cc = 0; cc < 3; cc++)
 #pragma unroll
-            for (int l = 0; l < 2; l++) {
-                acc += dsr[l] * (s0x[c] + (R)0.5 * dsx[c]);
-                const double inva = ar / ((double)(jmin + l) + 0.5);
-                red_add(S.f.jr + b + (long long)c * geo.P + l, qf * (double)acc * inva);
+                    for (int l = 0; l < 3; l++)
+                        atom_add(S.f.dq + bb + cc * geo.P + l,
+                                 -(double)w * (double)(s1x[cc] * s1r[l] - s0x[cc] * s0r[l]));
             }
+            const int irel_next = ib - snext;
+            const bool dead = irel_next < 0 || irel_next >= geo.nx || r1 >= rmax;
+            P.ix[k] = dead ? kDead : ix + di;
+            P.ox[k] = ox1;
+            P.y[k] = y1;
+            P.z[k] = z1;
         }
-        if (S.ph.track_dq) {
-            const double qw = -(double)w;
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-#pragma unroll
-                for (int l = 0; l < 3; l++)
-                    red_add(S.f.dq + b + (long long)c * geo.P + l,
-                            qw * (double)(s1x[c] * s1r[l] - s0x[c] * s0r[l]));
+        {
+            const bool head = run_sum_bounded<4, 2>(key, v, bnd);
+            const R tr = tjr[jrow];
+            double *const addr[4] = {S.f.jx + b, S.f.jx + b + 1, S.f.jr + b, S.f.jr + b + geo.P};
+            const R fac[4] = {tjx[jrow], tjx[jrow + 1], tr, tr};
+            group_atomics(key, head, v, addr, fac);
         }
-        const int irel_next = ib - snext;
-        const bool dead = irel_next < 0 || irel_next >= geo.nx || (double)r1 >= rmax;
-        P.ix[k] = dead ? kDead : ix + di;
-        P.ox[k] = ox1;
-        P.y[k] = y1;
-        P.z[k] = z1;
+        cur = nxt;
     }
 }
 
-}  // namespace
-
-
-
-namespace {
 template <class R>
 __global__ void k_load_columns(SimDev<R> S, const int *__restrict__ colbase, int ncols, int total) {
     const long long s = S.d->shift;
@@ -256,18 +446,44 @@ __global__ void k_load_columns(SimDev<R> S, const int *__restrict__ colbase, int
         lattice_particle<R>(S, s + lo, t - colbase[lo], t);
     }
 }
-}  // namespace
 
 inline int pgrid(int n) {
     int b = (n + TPB - 1) / TPB;
     return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
 }
 
+// Blocks of a particle kernel that are resident on the whole device at once (the kernels
+// loop over particle groups, so one resident wave is enough); cached per kernel address
+// (kernels of one signature share a function type, so the address is the key).
+template <class K> int resident_blocks(K *kernel) {
+    static std::mutex lock;
+    static const void *keys[8] = {};
+    static int vals[8] = {};
+    std::lock_guard<std::mutex> g(lock);
+    for (int q = 0; q < 8; q++)
+        if (keys[q] == (const void *)kernel) return vals[q];
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, TPB, 0);
+    const int v = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+    for (int q = 0; q < 8; q++)
+        if (!keys[q]) { keys[q] = (const void *)kernel; vals[q] = v; break; }
+    return v;
+}
+
+inline int particle_grid(int np_upper, int resident) {
+    const int need = (np_upper + TPB - 1) / TPB;
+    return need < 1 ? 1 : (need < resident ? need : resident);
+}
+
+}  // namespace
+
 template <class R> void launch_pass_a(const SimDev<R> &S, int np_upper, cudaStream_t st) {
-    k_pass_a<R><<<pgrid(np_upper), TPB, 0, st>>>(S);
+    k_pass_a<R><<<particle_grid(np_upper, resident_blocks(k_pass_a<R>)), TPB, 0, st>>>(S);
 }
 template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st) {
-    k_pass_b<R><<<pgrid(np_upper), TPB, 0, st>>>(S);
+    k_pass_b<R><<<particle_grid(np_upper, resident_blocks(k_pass_b<R>)), TPB, 0, st>>>(S);
 }
 template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_colbase, int ncols,
                                             int total, cudaStream_t st) {

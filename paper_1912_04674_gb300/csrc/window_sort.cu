@@ -8,64 +8,73 @@ namespace {
 
 constexpr int TPB = 256;
 
-// After step n: if the window shifts (paper Sec. 4 runs use a window moving at c), the live
-// window slides one physical column, the guard columns of the persistent arrays on both
-// sides of the new window are zeroed (the new front column of A and Er is among them), and
-// the new last cell column is filled with the plasma lattice at slots [np, np+count).
-template <class R> __global__ void k_window(SimDev<R> S) {
-    const long long n = S.d->step, s = S.d->shift;
-    if (!window_shifts(S.ph, n, s)) return;
-    const Geo g = S.geo;
-    const int noff = S.d->off + 1;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    // columns i in [-kG, -1] and [nx, nx+kG] of the new window
-    const int ncz = 2 * kG + 1;
-    for (int t = tid; t < ncz * g.P; t += nth) {
-        const int c = t / g.P, j = t - c * g.P;
-        const int i = c < kG ? c - kG : g.nx + (c - kG);
-        const long long id = g.at(noff, i, j);
-        S.f.ex[id] = (R)0;
-        S.f.er[id] = (R)0;
-        S.f.bt[id] = (R)0;
-        typename Cplx<R>::t zc;
-        zc.x = (R)0;
-        zc.y = (R)0;
-        S.f.a[0][id] = zc;
-        S.f.a[1][id] = zc;
-    }
-    if (!S.ph.have_plasma) return;
-    const long long c = s + 1 + g.nx - 1;  // lab column of the new last cell column
+// Injected particles in the new last cell column of lab column c.
+__device__ __forceinline__ int column_count(const Phys &ph, long long c, int nr) {
     int nv = 0;
-    for (int a = 0; a < S.ph.ppcx; a++)
-        if (plasma_density(S.ph, ((double)c + (a + 0.5) / S.ph.ppcx) * S.ph.dx) > 0.0) nv++;
-    const int count = nv * S.ph.ppcr * S.ph.ppct * g.nr;
-    const int np = S.d->np;
-    if (np + count > S.ph.cap) {
-        if (tid == 0) atomicOr(&S.d->err, (int)ERR_CAPACITY);
-        return;
-    }
-    for (int t = tid; t < count; t += nth) lattice_particle<R>(S, c, t, np + t);
+    for (int a = 0; a < ph.ppcx; a++)
+        if (plasma_density(ph, lattice_x(ph, c, a)) > 0.0) nv++;
+    return nv * ph.ppcr * ph.ppct * nr;
 }
 
-// Advance the counters after the window kernel (a separate launch, so that every thread of
-// the window kernel saw the same counters).
-template <class R> __global__ void k_advance(SimDev<R> S) {
-    Desc *d = S.d;
-    const long long n = d->step, s = d->shift;
-    d->last_shift = window_shifts(S.ph, n, s) ? 1 : 0;
-    if (d->last_shift) {
-        if (S.ph.have_plasma && !(d->err & ERR_CAPACITY)) {
-            const long long c = s + S.geo.nx;
-            int nv = 0;
-            for (int a = 0; a < S.ph.ppcx; a++)
-                if (plasma_density(S.ph, ((double)c + (a + 0.5) / S.ph.ppcx) * S.ph.dx) > 0.0) nv++;
-            d->np += nv * S.ph.ppcr * S.ph.ppct * S.geo.nr;
+// End of step n.  If the window shifts (paper Sec. 4 runs use a window moving at c), the live
+// window slides one physical column, the guard columns of the persistent arrays on both
+// sides of the new window are zeroed (the new front column of A and Er is among them), and
+// the new last cell column is filled with the plasma lattice at slots [np, np+count).  The
+// last block to finish then advances the counters (no block waits for another).
+template <class R> __global__ void k_window(SimDev<R> S) {
+    const long long n = S.d->step, s = S.d->shift;
+    const bool shifting = window_shifts(S.ph, n, s);
+    const Geo g = S.geo;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int np = S.d->np;
+    const long long c = s + g.nx;  // lab column of the new last cell column
+    int count = 0;
+    bool inject = false;
+    if (shifting) {
+        const int noff = S.d->off + 1;
+        // columns i in [-kG, -1] and [nx, nx+kG] of the new window
+        const int ncz = 2 * kG + 1;
+        for (int t = tid; t < ncz * g.P; t += nth) {
+            const int cc = t / g.P, j = t - cc * g.P;
+            const int i = cc < kG ? cc - kG : g.nx + (cc - kG);
+            const long long id = g.at(noff, i, j);
+            S.f.ex[id] = (R)0;
+            S.f.er[id] = (R)0;
+            S.f.bt[id] = (R)0;
+            typename Cplx<R>::t zc;
+            zc.x = (R)0;
+            zc.y = (R)0;
+            S.f.a[0][id] = zc;
+            S.f.a[1][id] = zc;
         }
-        d->shift = s + 1;
-        d->off += 1;
+        if (S.ph.have_plasma) {
+            count = column_count(S.ph, c, g.nr);
+            inject = np + count <= S.ph.cap;
+            if (inject)
+                for (int t = tid; t < count; t += nth) lattice_particle<R>(S, c, t, np + t);
+        }
     }
-    d->step = n + 1;
-    d->abuf ^= 1;
+    // last block: advance the counters once every block is done with them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&S.d->done, 1u);
+        if (prev == gridDim.x - 1) {
+            Desc *d = S.d;
+            d->done = 0;
+            d->last_shift = shifting ? 1 : 0;
+            if (shifting) {
+                if (S.ph.have_plasma) {
+                    if (inject) d->np = np + count;
+                    else d->err |= ERR_CAPACITY;
+                }
+                d->shift = s + 1;
+                d->off += 1;
+            }
+            d->step = n + 1;
+            d->abuf ^= 1;
+        }
+    }
 }
 
 // ---- counting sort by window cell (x-major, r fastest, like the grid) -------------------
@@ -74,14 +83,14 @@ template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *coun
     const int np = S.d->np;
     const long long s = S.d->shift;
     const int ncell = S.geo.nx * S.geo.nr;
-    const double idr = 1.0 / S.ph.dr;
+    const R idr = S.k.idr;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
         const int ix = P.ix[k];
         int c;
         if (ix == kDead) {
             c = ncell;
         } else {
-            const double y = (double)P.y[k], z = (double)P.z[k];
+            const R y = P.y[k], z = P.z[k];
             int j = (int)(sqrt(y * y + z * z) * idr);
             j = min(max(j, 0), S.geo.nr - 1);
             int i = (int)((long long)ix - s);
@@ -89,7 +98,9 @@ template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *coun
             c = i * S.geo.nr + j;
         }
         key[k] = c;
-        atomicAdd(count + c, 1);
+        // particles are near-sorted: one atomic per group of lanes with the same cell
+        const unsigned grp = __match_any_sync(__activemask(), c);
+        if ((int)(__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicAdd(count + c, __popc(grp));
     }
 }
 
@@ -173,8 +184,14 @@ __global__ void k_sort_scatter(SimDev<R> S, const int *key, int *cursor) {
     const int ncell = S.geo.nx * S.geo.nr;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
         const int c = key[k];
+        // one atomic per group of lanes with the same cell; ranks within the group by lane
+        const unsigned grp = __match_any_sync(__activemask(), c);
+        const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+        int base = 0;
+        if (lane == leader && c != ncell) base = atomicAdd(cursor + c, __popc(grp));
+        base = __shfl_sync(grp, base, leader);
         if (c == ncell) continue;  // dead: dropped
-        const int d = atomicAdd(cursor + c, 1);
+        const int d = base + __popc(grp & ((1u << lane) - 1u));
         out.ix[d] = P.ix[k];
         out.ox[d] = P.ox[k];
         out.y[d] = P.y[k];
@@ -206,10 +223,10 @@ inline int pgrid(int n) {
 template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st) {
     int work = (2 * kG + 1) * S.geo.P;
     if (inj_upper > work) work = inj_upper;
-    k_window<R><<<pgrid(work), TPB, 0, st>>>(S);
-}
-template <class R> void launch_advance(const SimDev<R> &S, cudaStream_t st) {
-    k_advance<R><<<1, 1, 0, st>>>(S);
+    // small blocks: the per-particle lattice arithmetic is FP64 and should spread over SMs
+    int blocks = (work + 63) / 64;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_window<R><<<blocks, 64, 0, st>>>(S);
 }
 
 // Exclusive scan of n <= SB*SI*SB*SI ints in place.
@@ -234,7 +251,6 @@ void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count, int *bl
 
 #define INST(R)                                                                          \
     template void launch_window<R>(const SimDev<R> &, int, cudaStream_t);                \
-    template void launch_advance<R>(const SimDev<R> &, cudaStream_t);                    \
     template void launch_sort<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t);
 INST(double)
 INST(float)
