@@ -232,6 +232,20 @@ def accuracy(k_total: int):
     return out
 
 
+def served_scan(n_jobs: int, rate: float = 2.0, budget_gb: float = 150.0):
+    """Served parametric scan: Poisson arrivals, jobs drawn like the scan workload, 500-3000
+    steps each, admission by device-memory budget, continuous batching (FP32_MIXED)."""
+    from paper_1912_04674_gb300 import serve
+    jobs = serve.poisson_jobs(n_jobs, rate)
+    srv = serve.ScanServer(int(budget_gb * 1e9), precision="fp32", max_slots=64, chunk_steps=25)
+    rep = srv.run(jobs)
+    rep.update({"arrival_rate_per_s": rate, "budget_gb": budget_gb,
+                "jobs_submitted": n_jobs, "steps_range": [500, 3000],
+                "workload": "scan jobs: Nx~U{256..2048}, Nr~U{64..256}, a0~U[0.5,3], "
+                            "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc"})
+    return rep
+
+
 def cpu_baseline(max_seconds=20.0):
     from oracle.oracle import OSim
     w = WORKLOAD
@@ -250,6 +264,24 @@ def cpu_baseline(max_seconds=20.0):
                       f"({units:.3g} particle-steps, {dt:.1f} s)"}
 
 
+def reduce_over_ranks(value: float, op: str, dist=None, device=None) -> float:
+    """MAX or SUM of a per-rank scalar over the process group (identity without one)."""
+    if dist is None or not dist.is_initialized():
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate(ms: float, units: float, dist=None, device=None) -> dict:
+    """Whole-job throughput of independent replicas: units summed over ranks, divided by
+    the slowest rank's time."""
+    ms_max = reduce_over_ranks(ms, "max", dist, device)
+    total = reduce_over_ranks(units, "sum", dist, device)
+    return {"ms_max": ms_max, "units": total, "value": total / (ms_max * 1e-3)}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -266,20 +298,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
     pk = peaks()
     result = {}
     plan = [("fp32", args.steps), ("fp64", max(3, args.steps // 8))]
@@ -294,10 +312,10 @@ def run_ours(args):
             ms, alive = timed_steps(sim, k)
         barrier()
         launches = sum(v[0] for v in sim.kernel_stats().values()) - launches0
-        ms_max = max_over_ranks(ms)
-        units = sum_over_ranks(alive * k)
+        agg = aggregate(ms, alive * k, dist, "cuda")
+        ms_max = agg["ms_max"]
         prof = kernel_profile(sim, max(3, min(k, 40)))
-        result[prec] = {"value": units / (ms_max * 1e-3), "ms_per_step": ms_max / k, "steps": k,
+        result[prec] = {"value": agg["value"], "ms_per_step": ms_max / k, "steps": k,
                         "alive": alive, "gpu_launches": launches, "clocks": cs.summary(),
                         "roofline": roofline(prof, prec, alive, pk),
                         "kernels": {n: round(v["ms_avg"], 4) for n, v in prof.items()}}
@@ -309,6 +327,7 @@ def run_ours(args):
     acc = accuracy(args.warmup + result["fp64"]["steps"]) if extras else None
     e2e = e2e_run("fp32", args.steps) if extras else None
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
+    scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
     elif rank == 0:
@@ -331,7 +350,7 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r32["gpu_launches"],
+            "cpu_baseline": cpu, "e2e": e2e, "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -384,6 +403,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--precision", choices=("both", "fp32", "fp64"), default="both",
                     help="time one path only (a profiling run, not a bench line)")
+    ap.add_argument("--scan-jobs", type=int, default=40,
+                    help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
     args = ap.parse_args()

@@ -117,8 +117,10 @@ typedef enum {
 lpic_status lpic_check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
                               char *msg, size_t msg_cap);
 
-/* Particle slots needed for plasma p on grid g: the full window plus the injection of
- * (sort_every + 2) window shifts between compactions.  0 for p == NULL. */
+/* Particle slots needed for plasma p on grid g: the full window, 10% more for electrons
+ * that travel with the window (trapped or pushed ahead of the pulse) while fresh plasma is
+ * injected, and the injection of (sort_every + 2) window shifts between compactions.
+ * 0 for p == NULL. */
 int64_t lpic_particle_capacity(const lpic_grid_params *g, const lpic_plasma_params *p);
 
 /* Bytes of the caller-owned device buffer for grid g (with g->particle_capacity) in

@@ -1,0 +1,85 @@
+"""Autotuner for the sort cadence of a simulation shape.
+
+The counting sort keeps particles ordered by cell so that warps gather from and deposit to
+few cells; sorting too often wastes bandwidth, too rarely lets particles drift apart.  For a
+shape (Nx, Nr, particles per cell, precision) the tuner times a short run of the real step
+for each candidate cadence on the current GPU and keeps the fastest in a JSON cache beside
+the built library.  Shapes are bucketed (Nx and Nr rounded to powers of two) so that a
+parameter scan reuses a handful of measurements.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(_HERE, "_build", "autotune.json")
+CANDIDATES = (5, 10, 20, 40)
+DEFAULT = 20
+_lock = threading.Lock()
+
+
+def _bucket(nx: int, nr: int, ppc: tuple, precision: str) -> str:
+    b = lambda v: 2 ** round(math.log2(max(v, 1)))  # noqa: E731
+    return f"{b(nx)}x{b(nr)}:{ppc[0]}x{ppc[1]}x{ppc[2]}:{precision}"
+
+
+def _load() -> dict:
+    try:
+        return json.load(open(CACHE))
+    except Exception:
+        return {}
+
+
+def cached_sort_every(nx: int, nr: int, ppc: tuple, precision: str) -> int | None:
+    return _load().get(_bucket(nx, nr, ppc, precision))
+
+
+def tune_sort_every(workload, precision: str = "fp32", steps: int = 40,
+                    candidates=CANDIDATES) -> int:
+    """Measure each candidate cadence on `workload` (a workloads.Workload) and cache the best."""
+    import dataclasses
+
+    import torch
+
+    from . import lpic as L
+
+    key = _bucket(workload.nx, workload.nr, workload.ppc, precision)
+    with _lock:
+        hit = _load().get(key)
+    if hit:
+        return int(hit)
+    best, best_ms = DEFAULT, float("inf")
+    for k in candidates:
+        w = dataclasses.replace(workload, sort_every=k)
+        sim = L.Simulation(L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, k),
+                           L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
+                           L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), precision=precision)
+        sim.step(2 * k)  # let the particles drift as they do between sorts
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(steps, 2 * k)
+        torch.cuda.synchronize()
+        a.record(sim.stream)
+        sim.step(n)
+        b.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        sim.close()
+        if ms < best_ms:
+            best, best_ms = k, ms
+    with _lock:
+        data = _load()
+        data[key] = best
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".tmp{os.getpid()}"
+        json.dump(data, open(tmp, "w"), indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+    return best
+
+
+def sort_every_for(nx: int, nr: int, ppc: tuple, precision: str) -> int:
+    """Cadence for a shape: the tuned value if one was measured for its bucket, else 20."""
+    v = cached_sort_every(nx, nr, ppc, precision)
+    return int(v) if v else DEFAULT

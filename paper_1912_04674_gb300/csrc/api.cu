@@ -117,7 +117,7 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
     L.count = take((ncell + 2) * 4);
     L.blocksum = take(((ncell + 1 + 4095) / 4096 + 1) * 4);
     L.blockcnt = take((cap / 256 + 2) * 4);
-    L.icount = take(16);
+    L.icount = take(((cap / 256 + 2) / 4096 + 4) * 4);   // count + scan block scratch
     L.diag = take(16 * 8);
     size_t col_bytes = (size_t)(g->nr + 1) * 16;
     size_t stage = kStageBytes;
@@ -390,7 +390,10 @@ lpic_status lpic_check_params(const lpic_grid_params *g, const lpic_plasma_param
 int64_t lpic_particle_capacity(const lpic_grid_params *g, const lpic_plasma_params *p) {
     if (!g || !p) return 0;
     const int64_t ppc = (int64_t)p->ppc_x * p->ppc_r * p->ppc_theta;
-    int64_t cap = (int64_t)g->nx * g->nr * ppc + 1024;
+    const int64_t full = (int64_t)g->nx * g->nr * ppc;
+    // electrons trapped in the wake or pushed ahead of the pulse ride with the window while
+    // fresh plasma keeps arriving: 10% over the full window
+    int64_t cap = full + full / 10 + 1024;
     if (g->moving_window) cap += (int64_t)(g->sort_every > 0 ? g->sort_every + 2 : 3) * g->nr * ppc;
     return cap;
 }

@@ -187,14 +187,19 @@ template <class R> __global__ void k_alive_count(SimDev<R> S, int *blockcnt) {
     const int c = __syncthreads_count(alive);
     if (threadIdx.x == 0) blockcnt[blockIdx.x] = c;
 }
-__global__ void k_scan_small(int *v, int n, int *total) {  // one thread; n is small
+// total = sum of the per-block counts; written before the in-place exclusive scan
+__global__ void k_sum_small(const int *v, int n, int *total) {
     int s = 0;
-    for (int k = 0; k < n; k++) {
-        int t = v[k];
-        v[k] = s;
-        s += t;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += v[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ int sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += sh[q];
+        *total = t;
     }
-    *total = s;
 }
 template <class R> __global__ void k_alive_write(SimDev<R> S, const int *blockbase, int *idx) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
@@ -322,7 +327,8 @@ void launch_alive_index(const SimDev<R> &S, int np_upper, int *idx, int *blockcn
                         cudaStream_t st) {
     const int nb = np_upper > 0 ? (np_upper + TPB - 1) / TPB : 1;
     k_alive_count<R><<<nb, TPB, 0, st>>>(S, blockcnt);
-    k_scan_small<<<1, 1, 0, st>>>(blockcnt, nb, d_count);
+    k_sum_small<<<1, 1024, 0, st>>>(blockcnt, nb, d_count);
+    scan_exclusive(blockcnt, nb, d_count + 1, st);   // d_count[1..] is the scan's block scratch
     k_alive_write<R><<<nb, TPB, 0, st>>>(S, blockcnt, idx);
 }
 template <class R>

@@ -203,6 +203,9 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
                                             int total, cudaStream_t st);
 template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
 
+// exclusive scan of n ints in place (n <= 4096 * 4096); blocksum: ceil(n/4096)+1 ints
+void scan_exclusive(int *data, int n, int *blocksum, cudaStream_t st);
+
 // counting sort by cell; `alt` receives the sorted particles; scratch ints:
 // key[cap], count[ncell+1], blocksum[...]
 template <class R> void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count,

@@ -98,9 +98,9 @@ def test_memory_plan_and_capacity(L):
     for w in (C1, C2):
         p = L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed)
         gs = L.grid_struct(L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every), p)
-        assert gs.particle_capacity >= w.particles + (w.sort_every + 2) * w.nr * 16
+        assert gs.particle_capacity >= 1.1 * w.particles + (w.sort_every + 2) * w.nr * 16
         b64 = L.lpic_required_bytes(gs, L.LPIC_FP64)
         b32 = L.lpic_required_bytes(gs, L.LPIC_FP32_MIXED)
         # two particle buffers dominate: 68 B (FP64) / 40 B (FP32) per slot
         assert b64 > 2 * 68 * gs.particle_capacity and b32 > 2 * 40 * gs.particle_capacity
-        assert b32 < b64 < 2 * 68 * gs.particle_capacity + 200e6
+        assert b32 < b64 < 2 * 68 * gs.particle_capacity + 400e6

@@ -139,3 +139,17 @@ def test_errors_are_reported_not_faulted():
     assert e.value.status == 1
     sim.step(3)                                    # vacuum, no particles: still runs
     assert sim.counters()["step"] == 3
+
+
+def test_window_slide_relocation_matches_oracle():
+    """A window of 20 cells shifted 64 times: the sliding live region reaches the end of
+    its allocation and is copied back twice; the state must not notice."""
+    w = dataclasses.replace(C1, name="reloc", nx=20, nr=12, ppc=(2, 2, 2), a0=0.6, w0=6.0,
+                            L=3.0, n0=0.01, sort_every=7)
+    o = oracle_from(w)
+    g = gpu_from(w)
+    for _ in range(8):
+        o.step(10)
+        g.step(10)
+        assert_parity(o, g, tol=1e-9)
+    assert o.shift >= 60
