@@ -131,11 +131,43 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- our arm
-def make_sim(prec: str, w=WORKLOAD):
+def make_sim(prec: str, w=WORKLOAD, sort_every=None):
     from paper_1912_04674_gb300 import lpic as L
-    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every)
+    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, sort_every or w.sort_every)
     return L.Simulation(g, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
                         L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), precision=prec)
+
+
+def settle(sim, n: int, chunk: int = 500):
+    """Untimed steps that bring the run to its developed state: after about Nx dx / (0.8 dx)
+    steps the window has moved past all plasma present at t = 0, and the timed steps see the
+    laser inside the wake it drives rather than a plasma at rest."""
+    done = 0
+    while done < n:
+        m = min(chunk, n - done)
+        sim.step(m)
+        done += m
+    sim.counters()  # synchronise and surface device errors
+
+
+STATE_FIELDS = ("ex", "er", "bt", "a", "am")
+
+
+def save_state(sim, path: str):
+    import numpy as np
+    p = sim.particles()
+    c = sim.counters()
+    np.savez(path, counters=np.array([c["step"], c["shift"]]), **{f"f_{n}": sim.field(n) for n in STATE_FIELDS},
+             **{f"p_{k}": v for k, v in p.items()})
+
+
+def load_state(sim, path: str):
+    import numpy as np
+    z = np.load(path if path.endswith(".npz") else path + ".npz")
+    sim.upload_counters(int(z["counters"][0]), int(z["counters"][1]))
+    for n in STATE_FIELDS:
+        sim.upload_field(n, z[f"f_{n}"])
+    sim.upload_particles({k[2:]: z[k] for k in z.files if k.startswith("p_")})
 
 
 def timed_steps(sim, k: int):
@@ -187,12 +219,13 @@ def roofline(prof: dict, prec: str, alive: float, pk: dict):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak else "none"}
 
 
-def e2e_run(prec: str, k: int):
-    """Same metric through the public API with host buffers: upload of the initial state from
+def e2e_run(prec: str, k: int, settle_steps: int):
+    """Same metric through the public API with host buffers: upload of a settled state from
     pinned host memory, then k steps each followed by a read of the on-axis wake."""
     import numpy as np
     import torch
     sim = make_sim(prec)
+    settle(sim, settle_steps)
     parts = sim.particles()
     fields = {n: sim.field(n) for n in ("ex", "er", "bt", "a", "am")}
     pin = {n: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for n, v in parts.items()}
@@ -201,6 +234,8 @@ def e2e_run(prec: str, k: int):
     alive = len(parts["x"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    c = sim.counters()
+    sim.upload_counters(c["step"], c["shift"])
     for n, v in pinf.items():
         sim.upload_field(n, v)
     sim.upload_particles(pin)
@@ -213,23 +248,42 @@ def e2e_run(prec: str, k: int):
     sim.close()
     return {"value": alive * k / dt, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d / k),
             "d2h_bytes_per_step": int(d2h / k), "steps": k,
-            "note": "initial-state upload amortised over the steps; wake read back every step"}
+            "note": "upload of a settled state amortised over the steps; wake read back every step"}
 
 
-def accuracy(k_total: int):
-    """FP32_MIXED vs FP64 on the same workload after k_total steps."""
+def accuracy(k_total: int, horizon: int = 300):
+    """FP32_MIXED against FP64 on the same workload, beside the FP64 run-to-run spread.
+
+    The a0 = 2 wake breaks and injects electrons after a few hundred steps; from then on the
+    run is chaotic: FP64 against itself with only the order of the atomic additions changed
+    (sort cadence 19 instead of 20) drifts from 1e-15 to percent level by the settled state.
+    The FP32 bar (1e-3 on wake Ex and peak |A|) is therefore checked at `horizon` steps,
+    inside the predictability horizon, and the settled-state errors are reported beside the
+    FP64 spread."""
     import numpy as np
-    s64, s32 = make_sim("fp64"), make_sim("fp32")
-    s64.step(k_total)
-    s32.step(k_total)
-    e64, e32 = s64.ex_axis(), s32.ex_axis()
-    a64, a32 = s64.a_abs_max(), s32.a_abs_max()
-    out = {"steps": k_total,
-           "wake_ex_rel_l2": float(np.linalg.norm(e32 - e64) / max(np.linalg.norm(e64), 1e-300)),
-           "a_max_rel": float(abs(a32 - a64) / a64)}
-    s64.close()
-    s32.close()
-    return out
+    s64, s64b, s32 = make_sim("fp64"), make_sim("fp64", sort_every=19), make_sim("fp32")
+
+    def errs():
+        e64 = s64.ex_axis()
+        n = max(np.linalg.norm(e64), 1e-300)
+        a64 = s64.a_abs_max()
+        return {"fp32_wake_ex_rel_l2": float(np.linalg.norm(s32.ex_axis() - e64) / n),
+                "fp32_a_max_rel": float(abs(s32.a_abs_max() / a64 - 1)),
+                "fp64_reordered_wake_ex_rel_l2": float(np.linalg.norm(s64b.ex_axis() - e64) / n),
+                "fp64_reordered_a_max_rel": float(abs(s64b.a_abs_max() / a64 - 1))}
+
+    for s in (s64, s64b, s32):
+        s.step(horizon)
+    at_h = errs()
+    for s in (s64, s64b, s32):
+        settle(s, k_total - horizon)
+    at_end = errs()
+    for s in (s64, s64b, s32):
+        s.close()
+    return {"horizon_steps": horizon,
+            "wake_ex_rel_l2": at_h["fp32_wake_ex_rel_l2"], "a_max_rel": at_h["fp32_a_max_rel"],
+            "within_1e-3": at_h["fp32_wake_ex_rel_l2"] <= 1e-3 and at_h["fp32_a_max_rel"] <= 1e-3,
+            "at_horizon": at_h, "settled_steps": k_total, "at_settled": at_end}
 
 
 def served_scan(n_jobs: int, rate: float = 2.0, budget_gb: float = 150.0):
@@ -305,6 +359,12 @@ def run_ours(args):
         plan = [p for p in plan if p[0] == args.precision]
     for prec, k in plan:
         sim = make_sim(prec)
+        if args.load_state:
+            load_state(sim, args.load_state)
+        else:
+            settle(sim, args.settle)
+        if args.save_state:
+            save_state(sim, args.save_state)
         sim.step(args.warmup)
         launches0 = sum(v[0] for v in sim.kernel_stats().values())
         barrier()
@@ -324,8 +384,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     extras = rank == 0 and not args.skip_extras and args.precision == "both"
-    acc = accuracy(args.warmup + result["fp64"]["steps"]) if extras else None
-    e2e = e2e_run("fp32", args.steps) if extras else None
+    acc = accuracy(args.settle + args.warmup + result["fp64"]["steps"]) if extras else None
+    e2e = e2e_run("fp32", args.steps, args.settle) if extras else None
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
@@ -339,6 +399,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "nr": w.nr, "particles": w.particles,
+                       "settle_steps": args.settle,
                        "ppc": list(w.ppc), "a0": w.a0, "w0": w.w0, "L": w.L, "n0": w.n0,
                        "ramp_cells": w.ramp_cells, "sort_every": w.sort_every,
                        "precision": "fp32_mixed (FP32 push/gather/stencils, FP64 axis rows and J/chi accumulation)",
@@ -403,6 +464,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--precision", choices=("both", "fp32", "fp64"), default="both",
                     help="time one path only (a profiling run, not a bench line)")
+    ap.add_argument("--settle", type=int, default=2600,
+                    help="untimed steps before the timed region (developed wake)")
+    ap.add_argument("--save-state", default=None, help="save the settled state (npz)")
+    ap.add_argument("--load-state", default=None, help="start from a saved state instead of settling")
     ap.add_argument("--scan-jobs", type=int, default=40,
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",

@@ -96,42 +96,59 @@ __device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V r
     oim = p * ry + pt * rx;
 }
 
-// Envelope solve on every node; A^{n+1} overwrites A^{n-1} in place (each node reads only
-// its own A^{n-1}); Phi^{n+1/2} = (Phi^n + Phi^{n+1})/2 for the position push.
+// Envelope solve on the off-axis nodes in the working precision; A^{n+1} overwrites A^{n-1}
+// in place (each node reads only its own A^{n-1}); Phi^{n+1/2} = (Phi^n + Phi^{n+1})/2 for the
+// position push.  The axis row is done in FP64 by the extra last column of blocks.
+template <class R> __device__ __forceinline__ void envelope_store(SimDev<R> &S, int id, int ab,
+                                                                  typename Cplx<R>::t c, R nre, R nim) {
+    typename Cplx<R>::t o;
+    o.x = nre;
+    o.y = nim;
+    S.f.a[ab ^ 1][id] = o;
+    S.f.phih[id] = (R)0.5 * ((R)0.5 * (c.x * c.x + c.y * c.y) + (R)0.5 * (nre * nre + nim * nim));
+}
+
+template <class R> __device__ __forceinline__ void envelope_axis_node(SimDev<R> &S, int i);
+
+// Blocks of the last grid column take the axis row (one node per warp row, FP64) so that
+// its long FP64 chains run spread over the SMs, beside the FP32 blocks.
 template <class R> __global__ void k_envelope(SimDev<R> S) {
     const Geo g = S.geo;
     const int off = S.d->off;
-    const int j = blockIdx.x * BX + threadIdx.x;
+    if (blockIdx.x == gridDim.x - 1) {
+        const int i = blockIdx.y * BY + threadIdx.y;
+        if (threadIdx.x == 0 && i <= g.nx) envelope_axis_node<R>(S, i);
+        return;
+    }
+    const int j = 1 + blockIdx.x * BX + threadIdx.x;
     const int i = blockIdx.y * BY + threadIdx.y;
     if (j > g.nr || i > g.nx) return;
     const int ab = S.d->abuf;
     const auto *A = S.f.a[ab];
-    auto *Am = S.f.a[ab ^ 1];
-    const long long id = g.at(off, i, j);
-    auto c = A[id];
-    auto xp = A[g.at(off, i + 1, j)];
-    auto xm = A[g.at(off, i - 1, j)];
-    auto rp = A[id + 1];
-    auto rm = (j > 0) ? A[id - 1] : c;
-    auto am = Am[id];
-    const double chi = S.f.chi[id];
-    R nre, nim;
+    const int id = g.at(off, i, j);
+    const auto c = A[id];
     const Kc<R> &K = S.k;
-    if (j == 0) {  // axis row in FP64
-        double dre, dim;
-        envelope_node<double>(c, xp, xm, rp, rm, am, chi, true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
-                              K.d_dt, K.d_dt2, K.d_envp, K.d_envpt, dre, dim);
-        nre = (R)dre;
-        nim = (R)dim;
-    } else {
-        envelope_node<R>(c, xp, xm, rp, rm, am, chi, false, K.idx2, K.idr2, K.tab[T_ENV1R * g.P + j],
-                         K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
-    }
-    typename Cplx<R>::t o;
-    o.x = nre;
-    o.y = nim;
-    Am[id] = o;
-    S.f.phih[id] = (R)0.5 * ((R)0.5 * (c.x * c.x + c.y * c.y) + (R)0.5 * (nre * nre + nim * nim));
+    R nre, nim;
+    envelope_node<R>(c, A[g.at(off, i + 1, j)], A[g.at(off, i - 1, j)], A[id + 1], A[id - 1],
+                     S.f.a[ab ^ 1][id], S.f.chi[id], false, K.idx2, K.idr2,
+                     K.tab[T_ENV1R * g.P + j], K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
+    envelope_store<R>(S, id, ab, c, nre, nim);
+}
+
+// The axis row j = 0 (even symmetry: radial part 4 (A_1 - A_0)/dr^2) in FP64, node (i, 0).
+template <class R> __device__ __forceinline__ void envelope_axis_node(SimDev<R> &S, int i) {
+    const Geo g = S.geo;
+    const int off = S.d->off;
+    const int ab = S.d->abuf;
+    const auto *A = S.f.a[ab];
+    const int id = g.at(off, i, 0);
+    const auto c = A[id];
+    const Kc<R> &K = S.k;
+    double dre, dim;
+    envelope_node<double>(c, A[g.at(off, i + 1, 0)], A[g.at(off, i - 1, 0)], A[id + 1], c,
+                          S.f.a[ab ^ 1][id], S.f.chi[id], true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
+                          K.d_dt, K.d_dt2, K.d_envp, K.d_envpt, dre, dim);
+    envelope_store<R>(S, id, ab, c, (R)dre, (R)dim);
 }
 
 // Ampere (Eq. MaxwellEqsCylindrical, second and third equations): Er on (i, j+1/2) with
@@ -221,7 +238,9 @@ template <class R> void launch_prepass(const SimDev<R> &S, cudaStream_t st) {
     k_prepass<R><<<grid2(S.geo.P, S.geo.nlive), dim3(BX, BY), 0, st>>>(S);
 }
 template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st) {
-    k_envelope<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);
+    dim3 g = grid2(S.geo.nr, S.geo.nx + 1);
+    g.x += 1;   // the axis-row blocks
+    k_envelope<R><<<g, dim3(BX, BY), 0, st>>>(S);
 }
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st) {
     k_ampere<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);

@@ -115,6 +115,18 @@ template <class R> struct SimDev {
 };
 
 // ---- shared device helpers -------------------------------------------------------------
+// Square roots and floors in the working precision, spelled out so that FP32 code never
+// takes a double-precision overload.
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+template <class R> __device__ __forceinline__ R sqrt_(R x);
+template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sqrt_<double>(double x) { return ::sqrt(x); }
+template <class R> __device__ __forceinline__ int floor_int(R x);
+template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
+template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
+
 __host__ __device__ __forceinline__ double plasma_density(const Phys &ph, double xlab) {
     if (xlab < ph.x_start) return 0.0;
     if (ph.ramp_len > 0.0 && xlab < ph.x_start + ph.ramp_len)

@@ -2,11 +2,11 @@
 // momentum push), pass B (time-centred position push, charge-conserving current deposit,
 // removal at the window edges) and the lattice loader.
 //
-// Work is split into warp-sized groups of consecutive particle slots (a warp-uniform loop,
-// so that every lane takes part in the warp-level reductions).  Particles are kept
+// Each block walks particle slots in block-sized groups (a block-uniform loop: every lane
+// takes part in the warp reductions and the blocks may synchronise).  Particles are kept
 // counting-sorted by cell, so runs of neighbouring lanes deposit onto the same nodes: each
-// deposit is first summed over its run with a segmented shuffle reduction (compensated
-// TwoSum in FP32), and only the run's first lane issues the FP64 global atomic.
+// deposit is first summed over its run with a segmented shuffle reduction (exact, in
+// integers, in FP32), and only one lane per run and deposit issues the FP64 global atomic.
 #include <mutex>
 
 #include "lpic_internal.cuh"
@@ -58,9 +58,7 @@ __device__ __forceinline__ R gather4(const R *__restrict__ F, const Geo &geo, in
            f * gw * f11;
 }
 
-template <class R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
-template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+
 
 // FP32 -> FP64 from the IEEE-754 field layouts with integer operations (the FP64 pipe is
 // slow on this part): exponent rebiased by 1023 - 127 = 896, mantissa widened.  FP32
@@ -82,97 +80,101 @@ __device__ __forceinline__ void atom_add(double *p, float v) {
     if (v != 0.0f) atomicAdd(p, f2d_bits(v));
 }
 
-// Sum of each deposit over the lanes of a warp that share its key (same target node);
-// returns true on one lane per key (the lowest), which then holds the sums.
-//  FP64: segmented shuffle sums over runs of consecutive lanes.
-//  FP32: exact integer accumulation -- each value is scaled by a power of two set by the
-//  largest exponent of its group (so that 32 of them cannot overflow 31 bits), rounded to an
-//  integer, summed exactly with one warp reduction, and scaled back: the group sum carries a
-//  single rounding of 2^-24 of the group's largest value.
-template <int N> __device__ __forceinline__ bool run_sum(unsigned key, double (&v)[N]) {
+// ---- warp runs ----------------------------------------------------------------------------
+// Particles are counting-sorted by cell, so lanes that deposit onto the same node sit next to
+// each other: a warp splits into a few runs of consecutive lanes with equal key.  Lane l's run
+// spans [head, end); lane l + o belongs to it iff l + o < end, so the segmented reductions
+// below need no per-step membership shuffles.
+struct Run {
+    int head, end;   // first lane and one past the last lane of this lane's run
+};
+__device__ __forceinline__ Run run_of(unsigned key) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned prev = __shfl_up_sync(FULL, key, 1);
-    const bool head = lane == 0 || prev != key;
-    const unsigned heads = __ballot_sync(FULL, head);
-    const int run = __popc(heads & (0xffffffffu >> (31u - lane)));
+    const unsigned heads = __ballot_sync(FULL, lane == 0u || prev != key);
+    const unsigned le = 0xffffffffu >> (31u - lane);          // lanes 0..lane
+    Run r;
+    r.head = 31 - __clz(heads & le);
+    const unsigned after = heads & ~le;
+    r.end = after ? __ffs(after) - 1 : 32;
+    return r;
+}
+
+// Segmented suffix sums: afterwards the head lane of each run holds the run's sums.
+template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r, T (&v)[N]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int orun = __shfl_down_sync(FULL, run, o);
-        const bool ok = lane + o < 32u && orun == run;
+        const bool in = lane + o < r.end;
 #pragma unroll
         for (int q = 0; q < N; q++) {
-            const double ov = __shfl_down_sync(FULL, v[q], o);
-            if (ok) v[q] += ov;
+            const T t = __shfl_down_sync(FULL, v[q], o);
+            if (in) v[q] += t;
         }
     }
-    return head;
 }
 
-template <int N> __device__ __forceinline__ bool run_sum(unsigned key, float (&v)[N]) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned grp = __match_any_sync(FULL, key);
-    const bool head = (unsigned)(__ffs(grp) - 1) == lane;
-#pragma unroll
-    for (int q = 0; q < N; q++) {
-        const unsigned e = ((unsigned)__float_as_int(v[q]) >> 23) & 0xffu;
-        const int emax = (int)__reduce_max_sync(grp, e);   // |v| < 2^(emax - 126)
-        const int ec = min(max(emax, 25), 254);
-        const float sc = __int_as_float((278 - ec) << 23);    // 2^(151 - emax)
-        const float isc = __int_as_float((ec - 24) << 23);    // 2^(emax - 151)
-        const int s = __reduce_add_sync(grp, __float2int_rn(v[q] * sc));   // |.| < 2^30
-        // groups below 2^-101 are dropped; a non-finite value makes the sum NaN
-        v[q] = emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)s * isc);
-    }
-    return head;
-}
-
-// As run_sum, for deposits whose magnitudes are bounded by per-lane values bnd[]: values
-// q < N/M share bound 0, the next N/M bound 1, ... (one exponent reduction per bound).
+// FP32 deposits are summed exactly: each value is scaled by a power of two set by the largest
+// exponent among the bounds of its run (so that 32 scaled values cannot overflow 31 bits),
+// rounded to an integer, summed exactly in integers, and scaled back at the head -- one
+// rounding of 2^-24 of the run's largest bound in all.  Values q in [m*N/M, (m+1)*N/M) share
+// bound m.  Runs whose bounds are all below 2^-101 deposit nothing; a non-finite value
+// makes the run's sums NaN.
 template <int N, int M>
-__device__ __forceinline__ bool run_sum_bounded(unsigned key, float (&v)[N], const float (&bnd)[M]) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned grp = __match_any_sync(FULL, key);
-    const bool head = (unsigned)(__ffs(grp) - 1) == lane;
+__device__ __forceinline__ void run_sums_exact(const Run &r, float (&v)[N], const float (&bnd)[M]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int m = 0; m < M; m++) {
-        const unsigned e = ((unsigned)__float_as_int(bnd[m]) >> 23) & 0xffu;
-        const int emax = (int)__reduce_max_sync(grp, e);   // every |v| of this bound < 2^(emax - 126)
-        const int ec = min(max(emax, 25), 254);
-        const float sc = __int_as_float((278 - ec) << 23);
-        const float isc = __int_as_float((ec - 24) << 23);
+        int e = (int)(((unsigned)__float_as_int(bnd[m]) >> 23) & 0xffu);
 #pragma unroll
-        for (int q = m * (N / M); q < (m + 1) * (N / M); q++) {
-            const int s = __reduce_add_sync(grp, __float2int_rn(v[q] * sc));
-            v[q] = emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)s * isc);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_down_sync(FULL, e, o);
+            if (lane + o < r.end) e = max(e, t);
         }
+        const int emax = __shfl_sync(FULL, e, r.head);      // |v| < 2^(emax - 126)
+        const int ec = min(max(emax, 25), 254);
+        const float sc = __int_as_float((278 - ec) << 23);   // 2^(151 - emax)
+        const float isc = __int_as_float((ec - 24) << 23);   // 2^(emax - 151)
+        int qi[N / M];
+#pragma unroll
+        for (int q = 0; q < N / M; q++) qi[q] = __float2int_rn(v[m * (N / M) + q] * sc);
+        run_sums<int, N / M>(r, qi);
+#pragma unroll
+        for (int q = 0; q < N / M; q++)
+            v[m * (N / M) + q] =
+                emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)qi[q] * isc);
     }
-    return head;
 }
 template <int N, int M>
-__device__ __forceinline__ bool run_sum_bounded(unsigned key, double (&v)[N], const double (&)[M]) {
-    return run_sum<N>(key, v);
+__device__ __forceinline__ void run_sums_exact(const Run &r, double (&v)[N], const double (&)[M]) {
+    run_sums<double, N>(r, v);
 }
 
-// After run_sum(_bounded) the group's sums v[0..3] sit on every lane of the group in FP32
-// (the integer reduction broadcasts), so the group's four atomics are issued by four of its
-// lanes at once.  In FP64 only the head holds them.  addr[q], fac[q]: target and row factor.
-__device__ __forceinline__ void group_atomics(unsigned key, bool head, const float (&v)[4],
-                                              double *const (&addr)[4], const float (&fac)[4]) {
+// The run's four deposits (sums at the head) go to addr[q] scaled by fac[q].  In FP32 a run of
+// four or more lanes spreads them over its first four lanes (one conversion and one atomic
+// each); shorter runs, and FP64, issue them from the head.
+__device__ __forceinline__ void run_atomics(const Run &r, unsigned key, const float (&v)[4],
+                                            double *const (&addr)[4], const float (&fac)[4]) {
+    const int lane = threadIdx.x & 31, rank = lane - r.head;
+    float s[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) s[q] = __shfl_sync(FULL, v[q], r.head);
     if (key == kNoKey) return;
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned grp = __match_any_sync(__activemask(), key);
-    const int gsize = __popc(grp), rank = __popc(grp & ((1u << lane) - 1u));
-    (void)head;
-    for (int q = rank; q < 4; q += gsize) {
-        const float val = q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
-        const float f = q == 0 ? fac[0] : q == 1 ? fac[1] : q == 2 ? fac[2] : fac[3];
-        double *const a = q == 0 ? addr[0] : q == 1 ? addr[1] : q == 2 ? addr[2] : addr[3];
-        atom_add(a, val * f);
+    if (r.end - r.head >= 4) {
+        if (rank < 4) {
+            const float val = rank == 0 ? s[0] * fac[0] : rank == 1 ? s[1] * fac[1]
+                            : rank == 2 ? s[2] * fac[2] : s[3] * fac[3];
+            double *const a = rank == 0 ? addr[0] : rank == 1 ? addr[1] : rank == 2 ? addr[2] : addr[3];
+            atom_add(a, val);
+        }
+    } else if (rank == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) atom_add(addr[q], s[q] * fac[q]);
     }
 }
-__device__ __forceinline__ void group_atomics(unsigned key, bool head, const double (&v)[4],
-                                              double *const (&addr)[4], const double (&fac)[4]) {
-    if (!head || key == kNoKey) return;
+__device__ __forceinline__ void run_atomics(const Run &r, unsigned key, const double (&v)[4],
+                                            double *const (&addr)[4], const double (&fac)[4]) {
+    if (key == kNoKey || (int)(threadIdx.x & 31) != r.head) return;
 #pragma unroll
     for (int q = 0; q < 4; q++) atom_add(addr[q], v[q] * fac[q]);
 }
@@ -182,16 +184,19 @@ template <class R> struct PReg {
     int ix;
     R ox, y, z, px, py, pz, w;
 };
-template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<R> &P, int k, int np) {
+// Slot k if k < lim (the end of the block's chunk), else an empty slot.
+template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<R> &P, int k, int lim) {
     PReg<R> q;
-    if (k < np) {
-        q.ix = P.ix[k];
-        q.ox = P.ox[k]; q.y = P.y[k]; q.z = P.z[k];
-        q.px = P.px[k]; q.py = P.py[k]; q.pz = P.pz[k]; q.w = P.w[k];
-    } else {
-        q.ix = kDead;
-        q.ox = q.y = q.z = q.px = q.py = q.pz = q.w = (R)0;
-    }
+    const bool in = k < lim;
+    const int kk = in ? k : 0;
+    q.ix = in ? P.ix[kk] : kDead;
+    q.ox = in ? P.ox[kk] : (R)0;
+    q.y = in ? P.y[kk] : (R)0;
+    q.z = in ? P.z[kk] : (R)0;
+    q.px = in ? P.px[kk] : (R)0;
+    q.py = in ? P.py[kk] : (R)0;
+    q.pz = in ? P.pz[kk] : (R)0;
+    q.w = in ? P.w[kk] : (R)0;
     return q;
 }
 
@@ -199,7 +204,9 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
 // Sec. 3; chi projected like a charge density divided by gamma, Sec. 2-3):
 //   g0 = sqrt(1+|p|^2+Phi), p* = p + dt/2 (qE - gradPhi/(2 g0)), gt = sqrt(1+|p*|^2+Phi),
 //   chi += q^2 w S/(gt V_chi),  F = qE - gradPhi/(2 gt),  Boris rotation with g- .
-template <class R> __global__ void __launch_bounds__(TPB) k_pass_a(SimDev<R> S) {
+// Every lane computes (a hole or a lane past the end works on harmless zeros or stale
+// values) and the results are masked, so the loop body has no data-dependent branch.
+template <class R> __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a(SimDev<R> S) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
@@ -207,84 +214,74 @@ template <class R> __global__ void __launch_bounds__(TPB) k_pass_a(SimDev<R> S) 
     const R hdt = S.k.hdt, idr = S.k.idr;
     const R *__restrict__ tchi = S.k.tab + T_CHI * geo.P;
     const R q = (R)-1;
-    const int lane = threadIdx.x & 31;
-    const int stride = ((gridDim.x * blockDim.x) >> 5) * 32;
-    int k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-    PReg<R> cur = load_particle<R>(P, k0 + lane, np);
-    for (; k0 < np; k0 += stride) {
-        const int k = k0 + lane;
-        const PReg<R> nxt = load_particle<R>(P, k + stride, np);   // prefetch
-        R v[4] = {0, 0, 0, 0}, bnd[1] = {0};
-        unsigned key = kNoKey;
-        int b = 0, jp = 0;
-        if (cur.ix != kDead) {
-            const int irel = (int)((long long)cur.ix - shift);
-            const R y = cur.y, z = cur.z, w = cur.w, px = cur.px, py = cur.py, pz = cur.pz;
-            const R r2 = y * y + z * z;
-            R r = (R)0, ct = (R)1, st = (R)0;
-            if (r2 > (R)0) {
-                const R ir = rsqrt_<R>(r2);
-                r = r2 * ir;
-                ct = y * ir;
-                st = z * ir;
-            }
-            const Loc<R> L = locate<R>(irel, cur.ox, r * idr, geo.nx, geo.nr);
-            const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
-            const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
-            const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
-            // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
-            b = geo.at(off, L.ip, L.jp);
-            const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
-            const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
-            const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
-            const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
-            const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
-            const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
-            const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
-            const R Ex = exg, Ey = erg * ct, Ez = erg * st;
-            const R By = -btg * st, Bz = btg * ct;               // Bx = 0
-            const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
+    // each block walks one contiguous chunk of slots, so that its successive iterations
+    // gather from neighbouring cells (field lines stay in L1)
+    const int chunk = ((np + gridDim.x - 1) / gridDim.x + TPB - 1) / TPB * TPB;
+    const int begin = blockIdx.x * chunk, end = min(begin + chunk, np);
+    int k = begin + threadIdx.x;
+    PReg<R> cur = load_particle<R>(P, k, end);
+    for (int base = begin; base < end; base += TPB, k += TPB) {
+        const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
+        const bool alive = cur.ix != kDead;
+        const int irel = (int)((long long)cur.ix - shift);
+        const R y = cur.y, z = cur.z, w = cur.w, px = cur.px, py = cur.py, pz = cur.pz;
+        const R r2 = y * y + z * z;
+        const bool onaxis = !(r2 > (R)0);
+        const R ir = onaxis ? (R)0 : rsqrt_<R>(r2);
+        const R r = r2 * ir, ct = onaxis ? (R)1 : y * ir, st = z * ir;
+        const Loc<R> L = locate<R>(irel, cur.ox, r * idr, geo.nx, geo.nr);
+        const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
+        const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
+        const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
+        // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
+        const int b = geo.at(off, L.ip, L.jp);
+        const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
+        const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
+        const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
+        const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
+        const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
+        const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
+        const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
+        const R Ex = exg, Ey = erg * ct, Ez = erg * st;
+        const R By = -btg * st, Bz = btg * ct;               // Bx = 0
+        const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
 
-            const R i2g0 = (R)0.5 * rsqrt_<R>((R)1 + px * px + py * py + pz * pz + phg);
-            const R sx = px + hdt * (q * Ex - Gx * i2g0);
-            const R sy = py + hdt * (q * Ey - Gy * i2g0);
-            const R sz = pz + hdt * (q * Ez - Gz * i2g0);
-            const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
+        const R i2g0 = (R)0.5 * rsqrt_<R>((R)1 + px * px + py * py + pz * pz + phg);
+        const R sx = px + hdt * (q * Ex - Gx * i2g0);
+        const R sy = py + hdt * (q * Ey - Gy * i2g0);
+        const R sz = pz + hdt * (q * Ez - Gz * i2g0);
+        const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
 
-            // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1); the 1/V factor
-            // is applied per row after the sum over lanes
-            const R base = w * rgt;
-            bnd[0] = base;
-            v[0] = base * w00;
-            v[1] = base * w10;
-            v[2] = base * w01;
-            v[3] = base * w11;
-            jp = L.jp;
-            key = (unsigned)b;
+        // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1); the 1/V factor
+        // is applied per row after the run sum
+        const R base_w = alive ? w * rgt : (R)0;
+        R v[4] = {base_w * w00, base_w * w10, base_w * w01, base_w * w11};
+        const R bnd[1] = {base_w};
+        const unsigned key = alive ? (unsigned)b : kNoKey;
 
-            const R i2gt = (R)0.5 * rgt;
-            const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
-            const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
-            const R tf = q * hdt * rsqrt_<R>((R)1 + mx * mx + my * my + mz * mz + phg);
-            const R ty = tf * By, tz = tf * Bz;                  // tx = 0
-            const R sf = (R)2 / ((R)1 + ty * ty + tz * tz);
-            const R vy = sf * ty, vz = sf * tz;
-            // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
-            const R ppx = mx + (my * tz - mz * ty);
-            const R ppy = my + (-mx * tz);
-            const R ppz = mz + (mx * ty);
+        const R i2gt = (R)0.5 * rgt;
+        const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
+        const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
+        const R tf = q * hdt * rsqrt_<R>((R)1 + mx * mx + my * my + mz * mz + phg);
+        const R ty = tf * By, tz = tf * Bz;                  // tx = 0
+        const R sf = (R)2 / ((R)1 + ty * ty + tz * tz);
+        const R vy = sf * ty, vz = sf * tz;
+        // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
+        const R ppx = mx + (my * tz - mz * ty);
+        const R ppy = my + (-mx * tz);
+        const R ppz = mz + (mx * ty);
+        if (alive) {
             P.px[k] = mx + (ppy * vz - ppz * vy) + hdt * Fx;
             P.py[k] = my + (-ppx * vz) + hdt * Fy;
             P.pz[k] = mz + (ppx * vy) + hdt * Fz;
         }
-        {
-            const bool head = run_sum_bounded<4, 1>(key, v, bnd);
-            const R i0 = tchi[jp], i1 = tchi[jp + 1];
-            double *const addr[4] = {S.f.chi + b, S.f.chi + b + geo.P, S.f.chi + b + 1,
-                                     S.f.chi + b + geo.P + 1};
-            const R fac[4] = {i0, i0, i1, i1};
-            group_atomics(key, head, v, addr, fac);
-        }
+        const Run run = run_of(key);
+        run_sums_exact<4, 1>(run, v, bnd);
+        const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
+        double *const addr[4] = {S.f.chi + b, S.f.chi + b + geo.P, S.f.chi + b + 1,
+                                 S.f.chi + b + geo.P + 1};
+        const R fac[4] = {i0, i0, i1, i1};
+        run_atomics(run, key, v, addr, fac);
         cur = nxt;
     }
 }
@@ -298,6 +295,60 @@ template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base,
     s[2] = lo ? (R)0 : f;
 }
 
+// Cell-crossing particles of one warp, parked until the warp can process 32 of them at once.
+constexpr int QW = 64;                 // entries per warp (at most 32 join per iteration)
+constexpr int NWARP = TPB / 32;
+template <class R> struct CrossQueue {
+    int ia[NWARP][QW], ja[NWARP][QW], di[NWARP][QW], dj[NWARP][QW];
+    R fa[NWARP][QW], fb[NWARP][QW], fra[NWARP][QW], frb[NWARP][QW], w[NWARP][QW];
+};
+
+// General charge-conserving deposit (3x3 window) of one crossing move.
+template <class R>
+__device__ __forceinline__ void deposit_general(const SimDev<R> &S, int off, int ia, int ib,
+                                                R fa, R fb, int ja, int jb, R fra, R frb, R w) {
+    const Geo &geo = S.geo;
+    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
+    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
+    const int imin = min(ia, ib), jmin = min(ja, jb);
+    R s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
+    shape3<R>(ia, fa, imin, s0x);
+    shape3<R>(ib, fb, imin, s1x);
+    shape3<R>(ja, fra, jmin, s0r);
+    shape3<R>(jb, frb, jmin, s1r);
+#pragma unroll
+    for (int cc = 0; cc < 3; cc++) { dsx[cc] = s1x[cc] - s0x[cc]; dsr[cc] = s1r[cc] - s0r[cc]; }
+    const int bb = geo.at(off, imin, jmin);
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+        R acc = (R)0;
+#pragma unroll
+        for (int cc = 0; cc < 2; cc++) {
+            acc += dsx[cc] * (s0r[l] + (R)0.5 * dsr[l]);
+            atom_add(S.f.jx + bb + cc * geo.P + l, w * acc * tjx[jmin + l]);
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; cc++) {
+        R acc = (R)0;
+#pragma unroll
+        for (int l = 0; l < 2; l++) {
+            acc += dsr[l] * (s0x[cc] + (R)0.5 * dsx[cc]);
+            atom_add(S.f.jr + bb + cc * geo.P + l, w * acc * tjr[jmin + l]);
+        }
+    }
+}
+
+// Process this warp's queued moves [0, n) (n is warp-uniform), one per lane at a time.
+template <class R>
+__device__ __forceinline__ void drain_queue(const SimDev<R> &S, int off, CrossQueue<R> &Q, int wq, int n) {
+    __syncwarp();
+    for (int t = threadIdx.x & 31; t < n; t += 32)
+        deposit_general<R>(S, off, Q.ia[wq][t], Q.ia[wq][t] + Q.di[wq][t], Q.fa[wq][t], Q.fb[wq][t],
+                           Q.ja[wq][t], Q.ja[wq][t] + Q.dj[wq][t], Q.fra[wq][t], Q.frb[wq][t], Q.w[wq][t]);
+    __syncwarp();
+}
+
 // Pass B: Phi^{n+1/2} at x^n, gbar = sqrt(1+|p|^2+Phi^{n+1/2}), x^{n+1} = x^n + dt p/gbar;
 // charge-conserving current in the (x, r) index plane (Esirkepov decomposition):
 //   Wx = DSx (S0r + DSr/2), Wr = DSr (S0x + DSx/2),
@@ -307,10 +358,12 @@ template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base,
 //   Jx(i+1/2, j)   ~ -w dx_ (1 - rbar),  Jx(i+1/2, j+1) ~ -w dx_ rbar,
 //   Jr(i, j+1/2)   ~ -w dr_ (1 - xbar),  Jr(i+1, j+1/2) ~ -w dr_ xbar,
 // (dx_, dr_ the in-cell displacements, xbar, rbar the mean fractions); those are summed over
-// the lanes sharing the cell before the atomics.  Cell-crossing particles take the 3x3
-// general form.  Particles leaving the next step's window (x < 0, x >= Nx dx) or reaching
-// r >= r_max are marked dead after their deposit.
-template <class R> __global__ void __launch_bounds__(TPB) k_pass_b(SimDev<R> S) {
+// the run of lanes sharing the cell before the atomics.  Cell-crossing particles (a few per
+// cent) are queued per warp in shared memory and take the 3x3 general form 32 at a time, so
+// that their slow path runs on full warps.  Particles leaving the next step's window (x < 0,
+// x >= Nx dx) or reaching r >= r_max are marked dead after their deposit.
+template <class R, bool DQ> __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b(SimDev<R> S) {
+    __shared__ CrossQueue<R> Q;
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
@@ -320,118 +373,103 @@ template <class R> __global__ void __launch_bounds__(TPB) k_pass_b(SimDev<R> S) 
     const R rmax = (R)(geo.nr * S.ph.dr);
     const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
     const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
-    const int lane = threadIdx.x & 31;
-    const int stride = ((gridDim.x * blockDim.x) >> 5) * 32;
-    int k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-    PReg<R> cur = load_particle<R>(P, k0 + lane, np);
-    for (; k0 < np; k0 += stride) {
-        const int k = k0 + lane;
-        const PReg<R> nxt = load_particle<R>(P, k + stride, np);   // prefetch
-        R v[4] = {0, 0, 0, 0}, bnd[2] = {0, 0};
-        unsigned key = kNoKey;
-        int b = 0, jrow = 0;
-        if (cur.ix != kDead) {
-            const int ix = cur.ix;
-            const int irel = (int)((long long)ix - shift);
-            const R ox = cur.ox, y = cur.y, z = cur.z, w = cur.w;
-            const R px = cur.px, py = cur.py, pz = cur.pz;
-            const R r0 = sqrt(y * y + z * z);
-            const R rn0 = r0 * idr;
-            const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
-            const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-            const R ig = rsqrt_<R>((R)1 + px * px + py * py + pz * pz + ph);   // 1/gbar
-            // The current is a difference of shape factors at two nearby positions: move x as
-            // an in-cell offset, and take the new radius as r^n plus the radial step in the
-            // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
-            R ox1 = ox + dtdx * px * ig;
-            const R dy = dt * py * ig, dz = dt * pz * ig;
-            const R y1 = y + dy, z1 = z + dz;
-            // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
-            // keep the 3-node shape window in range for non-finite input
-            int di = min(max((int)floor(ox1), -1), 1);
-            ox1 -= (R)di;
-            if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
-            const int ia = L.ip, ib = L.ip + di;
-            const R r1 = sqrt(y1 * y1 + z1 * z1);
-            const R rsum = r0 + r1;
-            const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
-            R rn1 = rn0 + step_r * idr;
-            if (rn1 < (R)0) rn1 = (R)0;
-            const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
-            const R fra = L.gp, frb = rn1 - (R)jb;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    int queued = 0;   // same value on every lane of the warp
+    // each block walks one contiguous chunk of slots (see pass A)
+    const int chunk = ((np + gridDim.x - 1) / gridDim.x + TPB - 1) / TPB * TPB;
+    const int begin = blockIdx.x * chunk, end = min(begin + chunk, np);
+    int k = begin + threadIdx.x;
+    PReg<R> cur = load_particle<R>(P, k, end);
+    for (int base = begin; base < end; base += TPB, k += TPB) {
+        const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
+        const bool alive = cur.ix != kDead;
+        const int ix = cur.ix;
+        const int irel = (int)((long long)ix - shift);
+        const R ox = cur.ox, y = cur.y, z = cur.z, w = cur.w;
+        const R px = cur.px, py = cur.py, pz = cur.pz;
+        const R r0 = sqrt_<R>(y * y + z * z);
+        const R rn0 = r0 * idr;
+        const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
+        const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
+        const R ig = rsqrt_<R>((R)1 + px * px + py * py + pz * pz + ph);   // 1/gbar
+        // The current is a difference of shape factors at two nearby positions: move x as
+        // an in-cell offset, and take the new radius as r^n plus the radial step in the
+        // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
+        R ox1 = ox + dtdx * px * ig;
+        const R dy = dt * py * ig, dz = dt * pz * ig;
+        const R y1 = y + dy, z1 = z + dz;
+        // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
+        // keep the 3-node shape window in range for non-finite input
+        int di = min(max(floor_int<R>(ox1), -1), 1);
+        ox1 -= (R)di;
+        if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
+        const int ia = L.ip;
+        const R r1 = sqrt_<R>(y1 * y1 + z1 * z1);
+        const R rsum = r0 + r1;
+        const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
+        R rn1 = rn0 + step_r * idr;
+        rn1 = rn1 < (R)0 ? (R)0 : rn1;
+        const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
+        const R fra = L.gp, frb = rn1 - (R)jb;
+        const bool stays = di == 0 && ja == jb;
 
-            if (ia == ib && ja == jb) {
-                const R ddx = ox1 - ox, ddr = frb - fra;
-                const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
-                bnd[0] = w * ddx;
-                bnd[1] = w * ddr;
-                v[0] = -bnd[0] * ((R)1 - rbar);
-                v[1] = -bnd[0] * rbar;
-                v[2] = -bnd[1] * ((R)1 - xbar);
-                v[3] = -bnd[1] * xbar;
-                b = geo.at(off, ia, ja);
-                jrow = ja;
-                key = (unsigned)b;
-            } else {
-                const int imin = min(ia, ib), jmin = min(ja, jb);
-                R s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
-                shape3<R>(ia, ox, imin, s0x);
-                shape3<R>(ib, ox1, imin, s1x);
-                shape3<R>(ja, fra, jmin, s0r);
-                shape3<R>(jb, frb, jmin, s1r);
+        const R ddx = ox1 - ox, ddr = frb - fra;
+        const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
+        const bool fast = alive && stays;
+        const R bx = fast ? w * ddx : (R)0, br = fast ? w * ddr : (R)0;
+        R v[4] = {-bx * ((R)1 - rbar), -bx * rbar, -br * ((R)1 - xbar), -br * xbar};
+        const R bnd[2] = {bx, br};
+        const int b = geo.at(off, ia, ja);
+        const unsigned key = fast ? (unsigned)b : kNoKey;
+
+        // queue the crossing moves in this warp's slots
+        const bool cross = alive && !stays;
+        const unsigned cm = __ballot_sync(FULL, cross);
+        if (cross) {
+            const int slot = queued + __popc(cm & ((1u << lane) - 1u));
+            Q.ia[wq][slot] = ia; Q.ja[wq][slot] = ja; Q.di[wq][slot] = di; Q.dj[wq][slot] = jb - ja;
+            Q.fa[wq][slot] = ox; Q.fb[wq][slot] = ox1; Q.fra[wq][slot] = fra; Q.frb[wq][slot] = frb;
+            Q.w[wq][slot] = w;
+        }
+        queued += __popc(cm);
+        // diagnostic only (a separate instantiation): charge change q w (S1 - S0), general form
+        if (DQ && alive) {
+            const int ib = ia + di, imin = min(ia, ib), jmin = min(ja, jb);
+            R s0x[3], s1x[3], s0r[3], s1r[3];
+            shape3<R>(ia, ox, imin, s0x);
+            shape3<R>(ib, ox1, imin, s1x);
+            shape3<R>(ja, fra, jmin, s0r);
+            shape3<R>(jb, frb, jmin, s1r);
+            const int bb = geo.at(off, imin, jmin);
 #pragma unroll
-                for (int cc = 0; cc < 3; cc++) { dsx[cc] = s1x[cc] - s0x[cc]; dsr[cc] = s1r[cc] - s0r[cc]; }
-                const int bb = geo.at(off, imin, jmin);
+            for (int cc = 0; cc < 3; cc++)
 #pragma unroll
-                for (int l = 0; l < 3; l++) {
-                    R acc = (R)0;
-#pragma unroll
-                    for (int cc = 0; cc < 2; cc++) {
-                        acc += dsx[cc] * (s0r[l] + (R)0.5 * dsr[l]);
-                        atom_add(S.f.jx + bb + cc * geo.P + l, w * acc * tjx[jmin + l]);
-                    }
-                }
-#pragma unroll
-                for (int cc = 0; cc < 3; cc++) {
-                    R acc = (R)0;
-#pragma unroll
-                    for (int l = 0; l < 2; l++) {
-                        acc += dsr[l] * (s0x[cc] + (R)0.5 * dsx[cc]);
-                        atom_add(S.f.jr + bb + cc * geo.P + l, w * acc * tjr[jmin + l]);
-                    }
-                }
-            }
-            if (S.ph.track_dq) {   // diagnostic: charge change q w (S1 - S0), general form
-                const int imin = min(ia, ib), jmin = min(ja, jb);
-                R s0x[3], s1x[3], s0r[3], s1r[3];
-                shape3<R>(ia, ox, imin, s0x);
-                shape3<R>(ib, ox1, imin, s1x);
-                shape3<R>(ja, fra, jmin, s0r);
-                shape3<R>(jb, frb, jmin, s1r);
-                const int bb = geo.at(off, imin, jmin);
-#pragma unroll
-                for (int cc = 0; cc < 3; cc++)
-#pragma unroll
-                    for (int l = 0; l < 3; l++)
-                        atom_add(S.f.dq + bb + cc * geo.P + l,
-                                 -(double)w * (double)(s1x[cc] * s1r[l] - s0x[cc] * s0r[l]));
-            }
-            const int irel_next = ib - snext;
+                for (int l = 0; l < 3; l++)
+                    atom_add(S.f.dq + bb + cc * geo.P + l,
+                             -(double)w * (double)(s1x[cc] * s1r[l] - s0x[cc] * s0r[l]));
+        }
+        if (alive) {
+            const int irel_next = ia + di - snext;
             const bool dead = irel_next < 0 || irel_next >= geo.nx || r1 >= rmax;
             P.ix[k] = dead ? kDead : ix + di;
             P.ox[k] = ox1;
             P.y[k] = y1;
             P.z[k] = z1;
         }
-        {
-            const bool head = run_sum_bounded<4, 2>(key, v, bnd);
-            const R tr = tjr[jrow];
-            double *const addr[4] = {S.f.jx + b, S.f.jx + b + 1, S.f.jr + b, S.f.jr + b + geo.P};
-            const R fac[4] = {tjx[jrow], tjx[jrow + 1], tr, tr};
-            group_atomics(key, head, v, addr, fac);
+        const Run run = run_of(key);
+        run_sums_exact<4, 2>(run, v, bnd);
+        const R tr = tjr[ja];
+        double *const addr[4] = {S.f.jx + b, S.f.jx + b + 1, S.f.jr + b, S.f.jr + b + geo.P};
+        const R fac[4] = {tjx[ja], tjx[ja + 1], tr, tr};
+        run_atomics(run, key, v, addr, fac);
+        // at most 32 join per iteration, so draining at 32 keeps the queue within QW
+        if (queued >= 32) {
+            drain_queue<R>(S, off, Q, wq, queued);
+            queued = 0;
         }
         cur = nxt;
     }
+    drain_queue<R>(S, off, Q, wq, queued);
 }
 
 template <class R>
@@ -483,7 +521,10 @@ template <class R> void launch_pass_a(const SimDev<R> &S, int np_upper, cudaStre
     k_pass_a<R><<<particle_grid(np_upper, resident_blocks(k_pass_a<R>)), TPB, 0, st>>>(S);
 }
 template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st) {
-    k_pass_b<R><<<particle_grid(np_upper, resident_blocks(k_pass_b<R>)), TPB, 0, st>>>(S);
+    if (S.ph.track_dq)
+        k_pass_b<R, true><<<particle_grid(np_upper, resident_blocks(k_pass_b<R, true>)), TPB, 0, st>>>(S);
+    else
+        k_pass_b<R, false><<<particle_grid(np_upper, resident_blocks(k_pass_b<R, false>)), TPB, 0, st>>>(S);
 }
 template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_colbase, int ncols,
                                             int total, cudaStream_t st) {

@@ -91,7 +91,7 @@ template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *coun
             c = ncell;
         } else {
             const R y = P.y[k], z = P.z[k];
-            int j = (int)(sqrt(y * y + z * z) * idr);
+            int j = (int)(sqrt_<R>(y * y + z * z) * idr);
             j = min(max(j, 0), S.geo.nr - 1);
             int i = (int)((long long)ix - s);
             i = min(max(i, 0), S.geo.nx - 1);
