@@ -300,6 +300,52 @@ def served_scan(n_jobs: int, rate: float = 2.0, budget_gb: float = 150.0):
     return rep
 
 
+def batched_scan(n_sims: int, steps: int, warmup: int = 5):
+    """Batched parametric scan (FP32_MIXED): n_sims uneven simulations drawn like the scan
+    workload, advanced together by one fused launch per phase per step.  Beside it, the same
+    simulations stepped by their own single-simulation launches on their own streams."""
+    import torch
+
+    from paper_1912_04674_gb300 import autotune, serve
+    from paper_1912_04674_gb300 import lpic as L
+    import workloads
+    jobs = workloads.scan_jobs(n_sims)
+    sims = [serve.make_simulation(w, "fp32", autotune.sort_every_for(w.nx, w.nr, w.ppc, "fp32"))
+            for w in jobs]
+    torch.cuda.synchronize()
+    b = L.Batch(sims)
+    b.step([warmup] * n_sims)
+    alive = sum(s.counters()["alive"] for s in sims)
+    l0 = b.launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(b.stream)
+    b.step([steps] * n_sims)
+    ev[1].record(b.stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    launches = b.launches() - l0
+    b.close()
+    # unfused: each simulation's own launches on its own stream, all streams in flight
+    k2 = max(3, steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k2):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    ms_streams = (time.perf_counter() - t0) * 1e3 / k2
+    for s in sims:
+        s.close()
+    torch.cuda.empty_cache()
+    return {"sims": n_sims, "steps": steps, "particles": alive, "ms_per_step": ms,
+            "value": alive / (ms * 1e-3), "unit": "particle-steps/s",
+            "gpu_launches_per_step": launches / steps,
+            "per_sim_streams_ms_per_step": ms_streams,
+            "workload": "64 scan sims: Nx~U{256..2048}, Nr~U{64..256}, a0~U[0.5,3], "
+                        "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc, FP32_MIXED, early steps"}
+
+
 def cpu_baseline(max_seconds=20.0):
     from oracle.oracle import OSim
     w = WORKLOAD
@@ -387,6 +433,7 @@ def run_ours(args):
     acc = accuracy(args.settle + args.warmup + result["fp64"]["steps"]) if extras else None
     e2e = e2e_run("fp32", args.steps, args.settle) if extras else None
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
+    batch = batched_scan(args.batch_sims, args.batch_steps) if (extras and args.batch_sims > 0) else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
@@ -411,7 +458,7 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "scan": scan, "gpu_launches": r32["gpu_launches"],
+            "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -468,6 +515,9 @@ def main():
                     help="untimed steps before the timed region (developed wake)")
     ap.add_argument("--save-state", default=None, help="save the settled state (npz)")
     ap.add_argument("--load-state", default=None, help="start from a saved state instead of settling")
+    ap.add_argument("--batch-sims", type=int, default=64,
+                    help="simulations in the batched-scan measurement (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=60)
     ap.add_argument("--scan-jobs", type=int, default=40,
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",

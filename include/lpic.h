@@ -202,17 +202,36 @@ lpic_status lpic_destroy(lpic_ctx *ctx);
 const char *lpic_last_error(const lpic_ctx *ctx);
 
 /* ---- batched form: many independent simulations advanced together ------------------
- * All contexts must share one precision and one device.  One step of the batch is a
- * fixed sequence of fused launches, each covering every simulation's grid tiles or
- * particle tiles through a work list, recorded once in a CUDA graph and replayed.
- * The contexts keep their own buffers; the batch allocates nothing on the device beyond
- * what lpic_batch_required_bytes() asks the caller for. */
-size_t lpic_batch_required_bytes(int n);
+ * The paper runs one simulation at a time; a parametric scan (a0, density, waist, grid
+ * size) is many independent runs of the same step (Sec. 2-3 equations, unchanged).  The
+ * batch advances them together: one step is a fixed sequence of fused persistent launches
+ * (prepass, pass A, envelope, pass B, Ampere, window), each walking a work list of
+ * {simulation, tile or block of particle slots} items over every active simulation,
+ * recorded once per set of active simulations in a CUDA graph and replayed.  Relocation
+ * and the periodic counting sort stay per simulation, on the batch stream.
+ * All contexts must share one precision and one device, be initialised
+ * (lpic_init_envelope done), and appear once.  The contexts keep their own buffers. */
+
+/* Device bytes the batch needs for its simulation views and work lists (0 if the
+ * contexts are invalid).  Depends on the contexts' shapes and the device's SM count. */
+size_t lpic_batch_required_bytes(lpic_ctx *const *ctxs, int n);
+
+/* device_buf: caller-owned, 256-byte aligned, at least lpic_batch_required_bytes bytes,
+ * alive and untouched until lpic_batch_destroy.  cuda_stream: the batch stream.
+ * Errors: LPIC_EINVAL (bad contexts or alignment), LPIC_ENOMEM_BUDGET (buffer too small),
+ * LPIC_ECUDA; the message is lpic_last_error(NULL). */
 lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, void *device_buf,
                               size_t buf_bytes, void *cuda_stream);
 /* Advance simulation k by steps_per_ctx[k] >= 0 steps; simulations with fewer steps
- * sit idle in the later launches.  Asynchronous on the batch stream. */
+ * drop out of the later launches (their items leave the work lists).  Asynchronous on the
+ * batch stream, ordered after earlier work on each context's stream; later calls on a
+ * context's stream are ordered after it.  Device-side errors of one simulation (particle
+ * capacity) are reported by that context's next lpic_diagnose. */
 lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
+/* Kernels the batch has enqueued so far (fused launches, relocations and sorts). */
+int64_t lpic_batch_launches(const lpic_batch *b);
+/* Message of the last failing call on b.  Never NULL. */
+const char *lpic_batch_last_error(const lpic_batch *b);
 lpic_status lpic_batch_destroy(lpic_batch *b);
 
 #ifdef __cplusplus

@@ -808,56 +808,164 @@ const char *lpic_last_error(const lpic_ctx *c) {
 }  // extern "C"
 
 // ============================================================================ batched form
+//
+// One step of a batch is a fixed sequence of fused launches (prepass, pass A, envelope,
+// pass B, Ampere, window), each a persistent grid walking a work list of items
+// {simulation, tile or virtual block, ...} over every active simulation.  The device buffer
+// the caller provides holds the SimDev views of the simulations followed by the work lists.
+// The sequence is recorded in a CUDA graph once per active set and replayed every step;
+// relocation of a slid-out window and the periodic sort stay per simulation, enqueued on the
+// batch stream between replays, because the host decides when they are due.
+
+namespace {
+constexpr int kBatchLists = 7;   // prepass, pass A, envelope, pass B, pass B (dq), ampere, window
+constexpr size_t kBatchAlign = 256;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 1024;   // generous bound when no device answers
+    return sms;
+}
+
+size_t sim_view_bytes(lpic_precision p) { return p == LPIC_FP64 ? sizeof(SimDev<double>) : sizeof(SimDev<float>); }
+
+int window_work(const lpic_ctx *c) {
+    int work = (2 * kG + 1) * c->geo.P;
+    const int inj = c->ph.have_plasma ? c->ph.ppcx * c->ph.ppcr * c->ph.ppct * c->geo.nr : 0;
+    return inj > work ? inj : work;
+}
+
+// Upper bound of the work items over all lists with every simulation active.
+size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
+    size_t items = 0;
+    for (int k = 0; k < n; k++) {
+        int tx, ty;
+        for (int ph = 0; ph < 3; ph++) {
+            grid_tiles(ctxs[k]->geo, ph, tx, ty);
+            items += (size_t)tx * ty;
+        }
+        items += (size_t)window_parts(ctxs[k]->geo, window_work(ctxs[k]));
+    }
+    // each particle list holds at most max(resident blocks, simulations) items; resident
+    // blocks of 256 threads are at most 8 per SM
+    const size_t per_list = (size_t)(8 * device_sms() > n ? 8 * device_sms() : n);
+    return items + 3 * per_list;
+}
+}  // namespace
 
 struct lpic_batch {
     std::vector<lpic_ctx *> ctx;
+    lpic_precision prec = LPIC_FP64;
     cudaStream_t st = nullptr;
-    std::vector<cudaStream_t> aux;
-    std::vector<cudaEvent_t> ev;
-    cudaEvent_t fork = nullptr;
+    char *dbuf = nullptr;
+    size_t items_off = 0, items_cap = 0;   // int4 slots after the views
+    cudaEvent_t ev = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<char> active_key;
-    std::vector<std::vector<long long>> per_replay;  // launches per graph replay, per context
+    int count[kBatchLists] = {};
+    size_t start[kBatchLists] = {};
+    int per_replay = 0;                     // fused launches per graph replay
+    long long launches = 0;                 // kernels enqueued by the batch (fused + per sim)
+    std::vector<int4> host_items;
     std::string err;
 };
 
 namespace {
 void batch_release(lpic_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    for (auto s : b->aux) cudaStreamDestroy(s);
-    for (auto e : b->ev) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev) cudaEventDestroy(b->ev);
 }
 
-// Record one step of every active simulation as parallel branches of one graph.
-lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
-    cudaEventRecord(b->fork, b->st);
-    for (size_t k = 0; k < b->ctx.size(); k++) {
-        if (!active[k]) continue;
-        lpic_ctx *c = b->ctx[k];
-        cudaStreamWaitEvent(b->aux[k], b->fork, 0);
-        const int npl = (int)c->g.particle_capacity, inj = inj_upper(c);
-        const bool timing = c->timing;
-        c->timing = false;
-        long long before[lpic_ctx::kFamilies];
-        memcpy(before, c->launches, sizeof before);
-        c->dispatch([&](auto &S) { enqueue_step_kernels(c, S, npl, inj, b->aux[k]); });
-        for (int f = 0; f < lpic_ctx::kFamilies; f++) {  // counted per replay instead
-            b->per_replay[k][f] = c->launches[f] - before[f];
-            c->launches[f] = before[f];
+// Work lists of the active simulations.  Particle lists split each simulation's slots into
+// virtual blocks in proportion to its capacity, at most one item per resident block in all
+// (so that one wave covers the list and no block takes two items while others idle).
+template <class R> void plan_items(lpic_batch *b, const std::vector<char> &active) {
+    const int n = (int)b->ctx.size();
+    std::vector<int4> L[kBatchLists];
+    int nact = 0;
+    long long total = 0;
+    for (int k = 0; k < n; k++)
+        if (active[k]) {
+            nact++;
+            total += b->ctx[k]->g.particle_capacity;
         }
-        c->timing = timing;
-        cudaEventRecord(b->ev[k], b->aux[k]);
-        cudaStreamWaitEvent(b->st, b->ev[k], 0);
+    const int gA = particle_multi_slots<R>(0, false);
+    for (int k = 0; k < n; k++) {
+        if (!active[k]) continue;
+        const lpic_ctx *c = b->ctx[k];
+        const int grid_list[3] = {0, 2, 5};
+        for (int ph = 0; ph < 3; ph++) {
+            int tx, ty;
+            grid_tiles(c->geo, ph, tx, ty);
+            for (int by = 0; by < ty; by++)
+                for (int bx = 0; bx < tx; bx++)
+                    L[grid_list[ph]].push_back(make_int4(k, bx, by, ph == 1 && bx == tx - 1 ? 1 : 0));
+        }
+        const long long cap = c->g.particle_capacity;
+        if (cap > 0) {
+            const bool dq = c->ph.track_dq != 0;
+            const int lists[2] = {1, dq ? 4 : 3};
+            const int slots[2] = {gA, particle_multi_slots<R>(1, dq)};
+            for (int q = 0; q < 2; q++) {
+                const long long room = slots[q] > nact ? slots[q] - nact : 1;
+                long long per = (total + room - 1) / room;
+                if (per < 256) per = 256;
+                const int nvb = (int)((cap + per - 1) / per);
+                for (int v = 0; v < nvb; v++) L[lists[q]].push_back(make_int4(k, v, nvb, 0));
+            }
+        }
+        const int parts = window_parts(c->geo, window_work(c));
+        for (int v = 0; v < parts; v++) L[6].push_back(make_int4(k, v, parts, 0));
     }
+    b->host_items.clear();
+    for (int q = 0; q < kBatchLists; q++) {
+        b->start[q] = b->host_items.size();
+        b->count[q] = (int)L[q].size();
+        b->host_items.insert(b->host_items.end(), L[q].begin(), L[q].end());
+    }
+}
+
+template <class R> SimDev<R> &view_of(lpic_ctx *c);
+template <> SimDev<double> &view_of<double>(lpic_ctx *c) { return c->sd; }
+template <> SimDev<float> &view_of<float>(lpic_ctx *c) { return c->sf; }
+
+// Upload the views and the work lists, then record one step of the active set.
+template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    plan_items<R>(b, active);
+    if (b->host_items.size() > b->items_cap) { b->err = "batch: work lists exceed the buffer"; return LPIC_EBUFSIZE; }
+    const int n = (int)b->ctx.size();
+    std::vector<SimDev<R>> views(n);
+    for (int k = 0; k < n; k++) views[k] = view_of<R>(b->ctx[k]);
+    const SimDev<R> *sims = (const SimDev<R> *)b->dbuf;
+    const int4 *items = (const int4 *)(b->dbuf + b->items_off);
+    // pageable sources: each copy returns once its source has been staged
+    cudaError_t e = cudaMemcpyAsync(b->dbuf, views.data(), n * sizeof(SimDev<R>), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess && !b->host_items.empty())
+        e = cudaMemcpyAsync(b->dbuf + b->items_off, b->host_items.data(), b->host_items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e != cudaSuccess) { b->err = std::string("batch upload: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+    int nl = 0;
+    auto it = [&](int q) { nl += b->count[q] > 0; return items + b->start[q]; };
+    launch_grid_multi<R>(0, sims, it(0), b->count[0], b->st);
+    launch_particles_multi<R>(0, false, sims, it(1), b->count[1], b->st);
+    launch_grid_multi<R>(1, sims, it(2), b->count[2], b->st);
+    launch_particles_multi<R>(1, false, sims, it(3), b->count[3], b->st);
+    launch_particles_multi<R>(1, true, sims, it(4), b->count[4], b->st);
+    launch_grid_multi<R>(2, sims, it(5), b->count[5], b->st);
+    launch_window_multi<R>(sims, it(6), b->count[6], b->st);
     e = cudaStreamEndCapture(b->st, &graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
+    b->per_replay = nl;
     b->active_key = active;
     return LPIC_OK;
 }
@@ -865,40 +973,45 @@ lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
 
 extern "C" {
 
-size_t lpic_batch_required_bytes(int n) {
-    (void)n;  // the graph form keeps everything in the contexts' own buffers
-    return 0;
+size_t lpic_batch_required_bytes(lpic_ctx *const *ctxs, int n) {
+    if (!ctxs || n <= 0) return 0;
+    for (int k = 0; k < n; k++)
+        if (!ctxs[k] || ctxs[k]->prec != ctxs[0]->prec) return 0;
+    return round_up((size_t)n * sim_view_bytes(ctxs[0]->prec), kBatchAlign) +
+           batch_items_bound(ctxs, n) * sizeof(int4);
 }
 
 lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, void *device_buf,
                               size_t buf_bytes, void *cuda_stream) {
-    (void)device_buf;
-    (void)buf_bytes;
     if (!out || !ctxs || n <= 0) { g_thread_err = "batch: bad arguments"; return LPIC_EINVAL; }
     for (int k = 0; k < n; k++)
-        if (!ctxs[k] || ctxs[k]->prec != ctxs[0]->prec) {
-            g_thread_err = "batch: contexts must be non-NULL and share one precision";
+        if (!ctxs[k] || ctxs[k]->prec != ctxs[0]->prec || !ctxs[k]->envelope_set) {
+            g_thread_err = "batch: contexts must be non-NULL, initialised and share one precision";
             return LPIC_EINVAL;
         }
+    for (int k = 0; k < n; k++)
+        for (int q = k + 1; q < n; q++)
+            if (ctxs[k] == ctxs[q]) { g_thread_err = "batch: a context appears twice"; return LPIC_EINVAL; }
+    const size_t need = lpic_batch_required_bytes(ctxs, n);
+    if (!device_buf || ((uintptr_t)device_buf % kBatchAlign) != 0) {
+        g_thread_err = "batch: device_buf must be non-NULL and 256-byte aligned";
+        return LPIC_EINVAL;
+    }
+    if (buf_bytes < need) { g_thread_err = "batch: device_buf smaller than lpic_batch_required_bytes"; return LPIC_ENOMEM_BUDGET; }
     lpic_batch *b = new lpic_batch();
     b->ctx.assign(ctxs, ctxs + n);
+    b->prec = ctxs[0]->prec;
     b->st = (cudaStream_t)cuda_stream;
-    b->aux.resize(n);
-    b->ev.resize(n);
-    b->per_replay.assign(n, std::vector<long long>(lpic_ctx::kFamilies, 0));
-    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-    for (int k = 0; k < n && e == cudaSuccess; k++) {
-        e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming);
-    }
+    b->dbuf = (char *)device_buf;
+    b->items_off = round_up((size_t)n * sim_view_bytes(b->prec), kBatchAlign);
+    b->items_cap = (buf_bytes - b->items_off) / sizeof(int4);
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         g_thread_err = std::string("batch: ") + cudaGetErrorString(e);
         batch_release(b);
         delete b;
         return LPIC_ECUDA;
     }
-    // the contexts' own streams must be idle before the batch stream takes over
-    for (int k = 0; k < n; k++) cudaStreamSynchronize(ctxs[k]->st);
     *out = b;
     return LPIC_OK;
 }
@@ -910,35 +1023,46 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps) {
         if (steps[k] < 0) { b->err = "batch: negative step count"; return LPIC_EINVAL; }
         if (steps[k] > maxs) maxs = steps[k];
     }
-    std::vector<char> active(b->ctx.size());
+    if (maxs == 0) return LPIC_OK;
     // order after earlier work on the contexts' own streams
     for (size_t k = 0; k < b->ctx.size(); k++) {
-        cudaEventRecord(b->ev[k], b->ctx[k]->st);
-        cudaStreamWaitEvent(b->st, b->ev[k], 0);
+        cudaEventRecord(b->ev, b->ctx[k]->st);
+        cudaStreamWaitEvent(b->st, b->ev, 0);
     }
+    std::vector<char> active(b->ctx.size());
     for (int t = 0; t < maxs; t++) {
         for (size_t k = 0; k < b->ctx.size(); k++) active[k] = steps[k] > t;
         for (size_t k = 0; k < b->ctx.size(); k++)
-            if (active[k]) pre_step(b->ctx[k], b->st);
+            if (active[k]) {
+                const long long r0 = b->ctx[k]->launches[F_RELOCATE];
+                pre_step(b->ctx[k], b->st);
+                b->launches += b->ctx[k]->launches[F_RELOCATE] - r0;
+            }
         if (!b->exec || active != b->active_key) {
-            lpic_status s = batch_capture(b, active);
+            lpic_status s = b->prec == LPIC_FP64 ? batch_capture<double>(b, active) : batch_capture<float>(b, active);
             if (s != LPIC_OK) return s;
         }
         cudaError_t e = cudaGraphLaunch(b->exec, b->st);
         if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        b->launches += b->per_replay;
         for (size_t k = 0; k < b->ctx.size(); k++)
-            if (active[k])
-                for (int f = 0; f < lpic_ctx::kFamilies; f++) b->ctx[k]->launches[f] += b->per_replay[k][f];
-        for (size_t k = 0; k < b->ctx.size(); k++)
-            if (active[k]) post_step(b->ctx[k], b->st);
+            if (active[k]) {
+                const long long s0 = b->ctx[k]->launches[F_SORT];
+                post_step(b->ctx[k], b->st);
+                b->launches += b->ctx[k]->launches[F_SORT] - s0;
+            }
     }
     // later calls on a context's own stream come after this batch step
-    cudaEventRecord(b->fork, b->st);
-    for (size_t k = 0; k < b->ctx.size(); k++) cudaStreamWaitEvent(b->ctx[k]->st, b->fork, 0);
+    cudaEventRecord(b->ev, b->st);
+    for (size_t k = 0; k < b->ctx.size(); k++) cudaStreamWaitEvent(b->ctx[k]->st, b->ev, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
     return LPIC_OK;
 }
+
+int64_t lpic_batch_launches(const lpic_batch *b) { return b ? b->launches : -1; }
+
+const char *lpic_batch_last_error(const lpic_batch *b) { return b ? b->err.c_str() : "batch: NULL"; }
 
 lpic_status lpic_batch_destroy(lpic_batch *b) {
     if (!b) return LPIC_EINVAL;

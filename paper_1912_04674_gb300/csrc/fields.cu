@@ -19,11 +19,12 @@ template <class R> __device__ __forceinline__ R sq(R v) { return v * v; }
 // gathers, Phi^n = |A^n|^2/2 (Sec. 2) and its centred differences (Sec. 3) on nodes, and
 // the clearing of the FP64 accumulators.  Every element of the live window incl. guards is
 // written, so the per-step arrays always read zero outside their valid range.
-template <class R> __global__ void k_prepass(SimDev<R> S) {
+// Tile (bx, by) of one simulation: threads run over j = bx*BX + tx, i = by*BY + ty - kG.
+template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> &S, int bx, int by) {
     const Geo g = S.geo;
     const int off = S.d->off;
-    const int j = blockIdx.x * BX + threadIdx.x;
-    const int i = (int)(blockIdx.y * BY + threadIdx.y) - kG;
+    const int j = bx * BX + threadIdx.x;
+    const int i = by * BY + (int)threadIdx.y - kG;
     if (j >= g.P || i > g.nx + kG) return;
     const long long id = g.at(off, i, j);
     const R dt = S.k.dt, idx_ = S.k.idx, idr = S.k.idr;
@@ -65,6 +66,8 @@ template <class R> __global__ void k_prepass(SimDev<R> S) {
     if (S.ph.track_dq) S.f.dq[id] = 0.0;
 }
 
+template <class R> __global__ void k_prepass(SimDev<R> S) { prepass_tile<R>(S, blockIdx.x, blockIdx.y); }
+
 // One node of Eq. (envelope_solver) in compute precision C:
 //   A^{n+1} = (1+i dt)/(1+dt^2) [2A^n - (1+i dt)A^{n-1} + dt^2 (lap A - chi A + 2i dA/dx)].
 // inv2rj = 1/(2 dr r_j) (unused on the axis row, whose radial part is 4 (A_1 - A_0)/dr^2).
@@ -99,7 +102,7 @@ __device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V r
 // Envelope solve on the off-axis nodes in the working precision; A^{n+1} overwrites A^{n-1}
 // in place (each node reads only its own A^{n-1}); Phi^{n+1/2} = (Phi^n + Phi^{n+1})/2 for the
 // position push.  The axis row is done in FP64 by the extra last column of blocks.
-template <class R> __device__ __forceinline__ void envelope_store(SimDev<R> &S, int id, int ab,
+template <class R> __device__ __forceinline__ void envelope_store(const SimDev<R> &S, int id, int ab,
                                                                   typename Cplx<R>::t c, R nre, R nim) {
     typename Cplx<R>::t o;
     o.x = nre;
@@ -108,20 +111,22 @@ template <class R> __device__ __forceinline__ void envelope_store(SimDev<R> &S, 
     S.f.phih[id] = (R)0.5 * ((R)0.5 * (c.x * c.x + c.y * c.y) + (R)0.5 * (nre * nre + nim * nim));
 }
 
-template <class R> __device__ __forceinline__ void envelope_axis_node(SimDev<R> &S, int i);
+template <class R> __device__ __forceinline__ void envelope_axis_node(const SimDev<R> &S, int i);
 
-// Blocks of the last grid column take the axis row (one node per warp row, FP64) so that
-// its long FP64 chains run spread over the SMs, beside the FP32 blocks.
-template <class R> __global__ void k_envelope(SimDev<R> S) {
+// Tile (bx, by): off-axis nodes j = 1 + bx*BX + tx, i = by*BY + ty; an axis tile takes the
+// axis row of columns by*BY + ty (one node per warp row, FP64), so that its long FP64 chains
+// run spread over the SMs beside the FP32 tiles.
+template <class R>
+__device__ __forceinline__ void envelope_tile(const SimDev<R> &S, int bx, int by, bool axis) {
     const Geo g = S.geo;
     const int off = S.d->off;
-    if (blockIdx.x == gridDim.x - 1) {
-        const int i = blockIdx.y * BY + threadIdx.y;
+    if (axis) {
+        const int i = by * BY + threadIdx.y;
         if (threadIdx.x == 0 && i <= g.nx) envelope_axis_node<R>(S, i);
         return;
     }
-    const int j = 1 + blockIdx.x * BX + threadIdx.x;
-    const int i = blockIdx.y * BY + threadIdx.y;
+    const int j = 1 + bx * BX + threadIdx.x;
+    const int i = by * BY + threadIdx.y;
     if (j > g.nr || i > g.nx) return;
     const int ab = S.d->abuf;
     const auto *A = S.f.a[ab];
@@ -135,8 +140,12 @@ template <class R> __global__ void k_envelope(SimDev<R> S) {
     envelope_store<R>(S, id, ab, c, nre, nim);
 }
 
+template <class R> __global__ void k_envelope(SimDev<R> S) {
+    envelope_tile<R>(S, blockIdx.x, blockIdx.y, blockIdx.x == gridDim.x - 1);
+}
+
 // The axis row j = 0 (even symmetry: radial part 4 (A_1 - A_0)/dr^2) in FP64, node (i, 0).
-template <class R> __device__ __forceinline__ void envelope_axis_node(SimDev<R> &S, int i) {
+template <class R> __device__ __forceinline__ void envelope_axis_node(const SimDev<R> &S, int i) {
     const Geo g = S.geo;
     const int off = S.d->off;
     const int ab = S.d->abuf;
@@ -153,11 +162,11 @@ template <class R> __device__ __forceinline__ void envelope_axis_node(SimDev<R> 
 
 // Ampere (Eq. MaxwellEqsCylindrical, second and third equations): Er on (i, j+1/2) with
 // Er = 0 on the x ends; Ex on (i+1/2, j) with the axis row 4 B_{1/2}/dr and Ex = 0 at r_max.
-template <class R> __global__ void k_ampere(SimDev<R> S) {
+template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &S, int bx, int by) {
     const Geo g = S.geo;
     const int off = S.d->off;
-    const int j = blockIdx.x * BX + threadIdx.x;
-    const int i = blockIdx.y * BY + threadIdx.y;
+    const int j = bx * BX + threadIdx.x;
+    const int i = by * BY + threadIdx.y;
     if (j > g.nr || i > g.nx) return;
     const long long id = g.at(off, i, j);
     const R dt = S.k.dt;
@@ -179,6 +188,31 @@ template <class R> __global__ void k_ampere(SimDev<R> S) {
             R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
             S.f.ex[id] += dt * (curl - (R)S.f.jx[id]);
         }
+    }
+}
+
+template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, blockIdx.x, blockIdx.y); }
+
+// Fused forms over a batch: each block walks work items {simulation, bx, by, flag}.
+template <class R>
+__global__ void __launch_bounds__(BX * BY) k_prepass_multi(const SimDev<R> *sims, const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        prepass_tile<R>(sims[it.x], it.y, it.z);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(BX * BY) k_envelope_multi(const SimDev<R> *sims, const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        envelope_tile<R>(sims[it.x], it.y, it.z, it.w != 0);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(BX * BY) k_ampere_multi(const SimDev<R> *sims, const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        ampere_tile<R>(sims[it.x], it.y, it.z);
     }
 }
 
@@ -257,7 +291,40 @@ template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStr
     k_set_off<R><<<1, 1, 0, st>>>(S, new_off);
 }
 
+// Tile grids of one simulation (the single-simulation launches use the same tiling).
+void grid_tiles(const Geo &g, int phase, int &tx, int &ty) {
+    if (phase == 0) { tx = (g.P + BX - 1) / BX; ty = (g.nlive + BY - 1) / BY; }          // prepass
+    else if (phase == 1) { tx = (g.nr + BX - 1) / BX + 1; ty = (g.nx + 1 + BY - 1) / BY; } // envelope
+    else { tx = (g.nr + 1 + BX - 1) / BX; ty = (g.nx + 1 + BY - 1) / BY; }               // ampere
+}
+
+template <class K> int resident(K *kernel, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+}
+
+template <class R>
+void launch_grid_multi(int phase, const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st) {
+    if (n <= 0) return;
+    static int res[3] = {0, 0, 0};
+    const dim3 blk(BX, BY);
+    if (phase == 0) {
+        if (!res[0]) res[0] = resident(k_prepass_multi<R>, BX * BY);
+        k_prepass_multi<R><<<n < res[0] ? n : res[0], blk, 0, st>>>(sims, items, n);
+    } else if (phase == 1) {
+        if (!res[1]) res[1] = resident(k_envelope_multi<R>, BX * BY);
+        k_envelope_multi<R><<<n < res[1] ? n : res[1], blk, 0, st>>>(sims, items, n);
+    } else {
+        if (!res[2]) res[2] = resident(k_ampere_multi<R>, BX * BY);
+        k_ampere_multi<R><<<n < res[2] ? n : res[2], blk, 0, st>>>(sims, items, n);
+    }
+}
+
 #define INST(R)                                                                              \
+    template void launch_grid_multi<R>(int, const SimDev<R> *, const int4 *, int, cudaStream_t); \
     template void launch_prepass<R>(const SimDev<R> &, cudaStream_t);                        \
     template void launch_envelope<R>(const SimDev<R> &, cudaStream_t);                       \
     template void launch_ampere<R>(const SimDev<R> &, cudaStream_t);                         \

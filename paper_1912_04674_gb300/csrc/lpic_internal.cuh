@@ -215,6 +215,22 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
                                             int total, cudaStream_t st);
 template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
 
+// ---- fused batch forms: one launch per phase over work items {sim, a, b, c} -------------
+// grid phases 0 prepass, 1 envelope (c = axis tile), 2 ampere: items {sim, bx, by, c}
+void grid_tiles(const Geo &g, int phase, int &tx, int &ty);
+template <class R>
+void launch_grid_multi(int phase, const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st);
+// particle phases (0 pass A, 1 pass B): items {sim, virtual block, virtual blocks of sim, 0}
+template <class R>
+void launch_particles_multi(int phase, bool dq, const SimDev<R> *sims, const int4 *items, int n,
+                            cudaStream_t st);
+// blocks of the fused particle kernel resident on the device at once (phase 0: pass A)
+template <class R> int particle_multi_slots(int phase, bool dq);
+// window: items {sim, part, parts of sim, 0}
+template <class R> void launch_window_multi(const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st);
+constexpr int kWindowThreads = 64;
+int window_parts(const Geo &g, int work);   // blocks of the single-simulation window launch
+
 // exclusive scan of n ints in place (n <= 4096 * 4096); blocksum: ceil(n/4096)+1 ints
 void scan_exclusive(int *data, int n, int *blocksum, cudaStream_t st);
 

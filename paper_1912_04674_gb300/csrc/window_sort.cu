@@ -21,11 +21,11 @@ __device__ __forceinline__ int column_count(const Phys &ph, long long c, int nr)
 // sides of the new window are zeroed (the new front column of A and Er is among them), and
 // the new last cell column is filled with the plasma lattice at slots [np, np+count).  The
 // last block to finish then advances the counters (no block waits for another).
-template <class R> __global__ void k_window(SimDev<R> S) {
+template <class R> __device__ __forceinline__ void window_body(const SimDev<R> &S, int part, int nparts) {
     const long long n = S.d->step, s = S.d->shift;
     const bool shifting = window_shifts(S.ph, n, s);
     const Geo g = S.geo;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int tid = part * blockDim.x + threadIdx.x, nth = nparts * blockDim.x;
     const int np = S.d->np;
     const long long c = s + g.nx;  // lab column of the new last cell column
     int count = 0;
@@ -59,7 +59,7 @@ template <class R> __global__ void k_window(SimDev<R> S) {
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&S.d->done, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == (unsigned)nparts - 1) {
             Desc *d = S.d;
             d->done = 0;
             d->last_shift = shifting ? 1 : 0;
@@ -74,6 +74,17 @@ template <class R> __global__ void k_window(SimDev<R> S) {
             d->step = n + 1;
             d->abuf ^= 1;
         }
+    }
+}
+
+template <class R> __global__ void k_window(SimDev<R> S) { window_body<R>(S, blockIdx.x, gridDim.x); }
+
+// Fused form over a batch: items {simulation, part, parts of that simulation}.
+template <class R> __global__ void k_window_multi(const SimDev<R> *sims, const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        window_body<R>(sims[it.x], it.y, it.z);
+        __syncthreads();   // the body's block-level bookkeeping must not overlap the next item
     }
 }
 
@@ -220,13 +231,20 @@ inline int pgrid(int n) {
 
 }  // namespace
 
+int window_parts(const Geo &g, int work) {
+    int blocks = (work + kWindowThreads - 1) / kWindowThreads;
+    return blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks);
+}
+
 template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st) {
     int work = (2 * kG + 1) * S.geo.P;
     if (inj_upper > work) work = inj_upper;
     // small blocks: the per-particle lattice arithmetic is FP64 and should spread over SMs
-    int blocks = (work + 63) / 64;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_window<R><<<blocks, 64, 0, st>>>(S);
+    k_window<R><<<window_parts(S.geo, work), kWindowThreads, 0, st>>>(S);
+}
+
+template <class R> void launch_window_multi(const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st) {
+    if (n > 0) k_window_multi<R><<<n < 152 * 8 ? n : 152 * 8, kWindowThreads, 0, st>>>(sims, items, n);
 }
 
 // Exclusive scan of n <= SB*SI*SB*SI ints in place.
@@ -251,6 +269,7 @@ void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count, int *bl
 
 #define INST(R)                                                                          \
     template void launch_window<R>(const SimDev<R> &, int, cudaStream_t);                \
+    template void launch_window_multi<R>(const SimDev<R> *, const int4 *, int, cudaStream_t); \
     template void launch_sort<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t);
 INST(double)
 INST(float)

@@ -76,9 +76,11 @@ _SIGS = {
     "lpic_envelope_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
     "lpic_destroy": (C.c_int, [C.c_void_p]),
     "lpic_last_error": (C.c_char_p, [C.c_void_p]),
-    "lpic_batch_required_bytes": (C.c_size_t, [C.c_int]),
+    "lpic_batch_required_bytes": (C.c_size_t, [C.POINTER(C.c_void_p), C.c_int]),
     "lpic_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpic_batch_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "lpic_batch_launches": (C.c_int64, [C.c_void_p]),
+    "lpic_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lpic_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
@@ -196,15 +198,18 @@ def lpic_last_error(ctx=None) -> str:
     return m.decode() if m else ""
 
 
-def lpic_batch_required_bytes(n: int) -> int:
-    return int(lib().lpic_batch_required_bytes(int(n)))
+def _ctx_array(ctxs):
+    return (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+
+
+def lpic_batch_required_bytes(ctxs) -> int:
+    return int(lib().lpic_batch_required_bytes(_ctx_array(ctxs), len(ctxs)))
 
 
 def lpic_batch_create(ctxs, device_ptr: int, nbytes: int, stream_ptr: int):
-    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
     out = C.c_void_p()
-    _check(lib().lpic_batch_create(C.byref(out), arr, len(ctxs), C.c_void_p(device_ptr), nbytes,
-                                   C.c_void_p(stream_ptr)))
+    _check(lib().lpic_batch_create(C.byref(out), _ctx_array(ctxs), len(ctxs), C.c_void_p(device_ptr),
+                                   nbytes, C.c_void_p(stream_ptr)))
     return out
 
 
@@ -212,11 +217,56 @@ def lpic_batch_step(batch, steps):
     arr = (C.c_int * len(steps))(*[int(s) for s in steps])
     st = lib().lpic_batch_step(batch, arr)
     if st != LPIC_OK:
-        raise LpicError(st, "batch step failed")
+        raise LpicError(st, lpic_batch_last_error(batch))
+
+
+def lpic_batch_launches(batch) -> int:
+    return int(lib().lpic_batch_launches(batch))
+
+
+def lpic_batch_last_error(batch) -> str:
+    m = lib().lpic_batch_last_error(batch)
+    return m.decode() if m else ""
 
 
 def lpic_batch_destroy(batch):
     _check(lib().lpic_batch_destroy(batch))
+
+
+class Batch:
+    """Owner of one lpic_batch over Simulation objects, with its device buffer from PyTorch."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+
+        self.sims = list(sims)
+        ctxs = [s.ctx for s in self.sims]
+        self.nbytes = lpic_batch_required_bytes(ctxs)
+        if self.nbytes == 0:
+            raise LpicError(1, "batch: contexts must be valid and share one precision")
+        dev = self.sims[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=dev)
+        ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        with torch.cuda.device(dev):
+            self.b = lpic_batch_create(ctxs, ptr, self.nbytes, self.stream.cuda_stream)
+
+    def step(self, steps):
+        lpic_batch_step(self.b, steps)
+
+    def launches(self) -> int:
+        return lpic_batch_launches(self.b)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            lpic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience owner ------------------------------------------------------------------------

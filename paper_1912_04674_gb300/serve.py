@@ -3,9 +3,10 @@
 Jobs (a0, density, waist, grid size, step count) arrive over time.  Each admitted job owns
 its simulation state on the device until it finishes (fields and particles stay resident);
 admission is by device-memory footprint (lpic_required_bytes) against a budget and by a
-slot count.  All running jobs advance together through one lpic_batch (one CUDA graph per
-step over every active simulation); jobs that arrive while others run are admitted at the
-next step boundary, and finished jobs retire there, freeing their memory for the queue.
+slot count.  All running jobs advance together through one lpic_batch (per step, one
+fused launch per phase over every active simulation, replayed from a CUDA graph); jobs
+that arrive while others run are admitted at the next step boundary, and finished jobs
+retire there, freeing their memory for the queue.
 The server records each job's time to result (completion minus arrival) and reports the
 p50/p99 latency, jobs/hour and aggregate particle-steps/s.
 
@@ -110,6 +111,7 @@ class ScanServer:
         self.particle_steps = 0.0
         self.max_running = 0
         self.rejected: list[Job] = []
+        self.launches = 0               # kernels enqueued by the batches
 
     # -- batch membership ----------------------------------------------------------------
     def _rebuild_batch(self):
@@ -118,11 +120,11 @@ class ScanServer:
         if key == self._batch_key:
             return
         if self._batch is not None:
-            L.lpic_batch_destroy(self._batch)
+            self.launches += self._batch.launches()
+            self._batch.close()
             self._batch = None
         if self.running:
-            self._batch = L.lpic_batch_create([r.sim.ctx for r in self.running], 0, 0,
-                                              self.stream.cuda_stream)
+            self._batch = L.Batch([r.sim for r in self.running], self.stream)
         self._batch_key = key
 
     def _admit(self, now: float):
@@ -202,7 +204,7 @@ class ScanServer:
                 break
             self._rebuild_batch()
             steps = [min(self.chunk, r.remaining) for r in self.running]
-            L.lpic_batch_step(self._batch, steps)
+            self._batch.step(steps)
             self.stream.synchronize()
             for r, s in zip(self.running, steps):
                 r.remaining -= s
@@ -212,7 +214,8 @@ class ScanServer:
                 # the contexts' own streams are ordered after the batch stream
                 self._retire(clock() - self.t0)
         if self._batch is not None:
-            L.lpic_batch_destroy(self._batch)
+            self.launches += self._batch.launches()
+            self._batch.close()
             self._batch = None
         torch.cuda.synchronize(self.device)
         return self.report(clock() - self.t0)
@@ -220,7 +223,7 @@ class ScanServer:
     def report(self, elapsed: float) -> dict:
         lat = np.array([j.latency for j in self.done if j.latency is not None])
         return {"jobs": len(self.done), "rejected": len(self.rejected), "elapsed_s": elapsed,
-                "max_concurrent": self.max_running,
+                "max_concurrent": self.max_running, "gpu_launches": self.launches,
                 "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
                 "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
                 "jobs_per_hour": len(self.done) / elapsed * 3600.0 if elapsed > 0 else None,

@@ -42,11 +42,13 @@ def test_batch_matches_alone(precision, tol):
         s.step(n)
         alone.append(s)
     mixed = [gpu_from(w, precision=precision) for w in jobs]
-    stream = torch.cuda.Stream()
-    b = L.lpic_batch_create([s.ctx for s in mixed], 0, 0, stream.cuda_stream)
-    L.lpic_batch_step(b, [10, 10, 10])          # all three together
-    L.lpic_batch_step(b, [20, 35, 10])          # uneven: later launches run fewer simulations
-    L.lpic_batch_destroy(b)
+    b = L.Batch(mixed, torch.cuda.Stream())
+    b.step([10, 10, 10])          # all three together
+    b.step([20, 35, 10])          # uneven: later launches run fewer simulations
+    # one fused launch per phase (pass B of the untracked simulations only) per step, plus
+    # the per-simulation sorts every 5 steps
+    assert b.launches() == 6 * 45 + sum(n // 5 * 6 for n in steps)
+    b.close()
     for a, m, n in zip(alone, mixed, steps):
         assert m.counters()["step"] == n
         for f in ("ex", "er", "bt", "a", "chi", "jx"):
