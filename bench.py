@@ -314,6 +314,7 @@ def batched_scan(n_sims: int, steps: int, warmup: int = 5):
             for w in jobs]
     torch.cuda.synchronize()
     b = L.Batch(sims)
+    tile, packs = autotune.tune_batch(b, "fp32")   # real steps of the batch, untimed
     b.step([warmup] * n_sims)
     alive = sum(s.counters()["alive"] for s in sims)
     l0 = b.launches()
@@ -340,7 +341,8 @@ def batched_scan(n_sims: int, steps: int, warmup: int = 5):
     torch.cuda.empty_cache()
     return {"sims": n_sims, "steps": steps, "particles": alive, "ms_per_step": ms,
             "value": alive / (ms * 1e-3), "unit": "particle-steps/s",
-            "gpu_launches_per_step": launches / steps,
+            "gpu_launches_per_step": launches / steps, "particles_per_item": tile, "packs": packs,
+            "tuning_ms_per_step": [[c, p, round(m, 3)] for c, p, m in getattr(b, "tuning_log", [])],
             "per_sim_streams_ms_per_step": ms_streams,
             "workload": "64 scan sims: Nx~U{256..2048}, Nr~U{64..256}, a0~U[0.5,3], "
                         "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc, FP32_MIXED, early steps"}

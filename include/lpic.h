@@ -228,6 +228,15 @@ lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, vo
  * context's stream are ordered after it.  Device-side errors of one simulation (particle
  * capacity) are reported by that context's next lpic_diagnose. */
 lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
+/* Tuning of the fused launches, effective at the next lpic_batch_step:
+ * particles_per_item: particle slots per work item of the fused particle passes (a
+ *   multiple of 256 in [1024, 1048576]; default 4096).  Smaller items balance the blocks
+ *   better, larger ones cost less per item.
+ * packs: split the simulations into this many packs (0: as few as the parameter space
+ *   allows, one per 56 simulations), each with its own launch sequence as a parallel branch
+ *   of the graph, so that phases of different packs overlap on the device.
+ * The binding's autotuner picks both by timing real steps.  Errors: LPIC_EINVAL. */
+lpic_status lpic_batch_set_tuning(lpic_batch *b, int32_t particles_per_item, int32_t packs);
 /* Kernels the batch has enqueued so far (fused launches, relocations and sorts). */
 int64_t lpic_batch_launches(const lpic_batch *b);
 /* Message of the last failing call on b.  Never NULL. */

@@ -1,8 +1,10 @@
 // Host side of the C ABI declared in include/lpic.h: parameter checks, memory planning
 // inside the caller's buffer, step orchestration, diagnostics, uploads, batched form.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -291,6 +293,9 @@ template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
         S.p[k].w = (R *)(b + L.parts[k][7]);
         S.p[k].id = (uint64_t *)(b + L.parts[k][8]);
     }
+    S.sb.key = (int *)(b + L.key);
+    S.sb.count = (int *)(b + L.count);
+    S.sb.blocksum = (int *)(b + L.blocksum);
 }
 
 lpic_status pull_desc(lpic_ctx *c) {
@@ -351,8 +356,8 @@ int inj_upper(const lpic_ctx *c) {
     return c->ph.have_plasma ? c->ph.ppcx * c->ph.ppcr * c->ph.ppct * c->geo.nr : 0;
 }
 
-// Host mirror update after one step's launches, and the periodic sort.
-void post_step(lpic_ctx *c, cudaStream_t st) {
+// Host mirror update for one step; true when the periodic sort follows the step.
+bool advance_mirror(lpic_ctx *c) {
     if (window_shifts(c->ph, c->step, c->shift)) {
         c->shift += 1;
         c->off += 1;
@@ -362,11 +367,19 @@ void post_step(lpic_ctx *c, cudaStream_t st) {
     }
     c->step += 1;
     if (c->g.particle_capacity > 0 && c->np_upper > 0 && ++c->since_sort >= c->g.sort_every) {
+        c->since_sort = 0;
+        return true;
+    }
+    return false;
+}
+
+// Host mirror update after one step's launches, and the periodic sort.
+void post_step(lpic_ctx *c, cudaStream_t st) {
+    if (advance_mirror(c)) {
         const int npl = launch_cap(c);
         traced(c, F_SORT, kSortLaunches, st, [&] {
             c->dispatch([&](auto &S) { launch_sort(S, npl, c->key, c->count, c->blocksum, st); });
         });
-        c->since_sort = 0;
     }
 }
 
@@ -811,33 +824,29 @@ const char *lpic_last_error(const lpic_ctx *c) {
 //
 // One step of a batch is a fixed sequence of fused launches (prepass, pass A, envelope,
 // pass B, Ampere, window), each a persistent grid walking a work list of items
-// {simulation, tile or virtual block, ...} over every active simulation.  The device buffer
-// the caller provides holds the SimDev views of the simulations followed by the work lists.
-// The sequence is recorded in a CUDA graph once per active set and replayed every step;
-// relocation of a slid-out window and the periodic sort stay per simulation, enqueued on the
-// batch stream between replays, because the host decides when they are due.
+// {simulation, tile or virtual block, ...} over the active simulations.  The simulations'
+// views travel in the launches' parameter space, up to kPackMax per launch; larger batches
+// are split into packs of near-equal size whose launch sequences run as parallel branches.
+// The device buffer the caller provides holds the work lists.  The sequence is recorded in a
+// CUDA graph once per active set and replayed every step; relocation of a slid-out window
+// and the periodic sort stay per simulation, enqueued on the batch stream between replays,
+// because the host decides when they are due.
 
 namespace {
-constexpr int kBatchLists = 7;   // prepass, pass A, envelope, pass B, pass B (dq), ampere, window
-constexpr size_t kBatchAlign = 256;
-
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int device_sms() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-        return 1024;   // generous bound when no device answers
-    return sms;
-}
-
-size_t sim_view_bytes(lpic_precision p) { return p == LPIC_FP64 ? sizeof(SimDev<double>) : sizeof(SimDev<float>); }
+// work lists: prepass, pass A (and the sort's count and scatter), envelope, pass B, pass B
+// (dq), ampere, window, sort counter blocks, one item per simulation
+constexpr int kBatchLists = 9;
+enum { BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_AMPERE, BL_WINDOW, BL_SORTBLK, BL_SIMS };
+constexpr int kDefaultChunk = 4096, kMinChunk = 1024, kMaxChunk = 1 << 20;
 
 int window_work(const lpic_ctx *c) {
     int work = (2 * kG + 1) * c->geo.P;
     const int inj = c->ph.have_plasma ? c->ph.ppcx * c->ph.ppcr * c->ph.ppct * c->geo.nr : 0;
     return inj > work ? inj : work;
 }
+
+int pack_count(int n) { return (n + kPackMax - 1) / kPackMax; }
+size_t flags_bytes(int n) { return ((size_t)n * sizeof(int) + 255) / 256 * 256; }
 
 // Upper bound of the work items over all lists with every simulation active.
 size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
@@ -849,11 +858,10 @@ size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
             items += (size_t)tx * ty;
         }
         items += (size_t)window_parts(ctxs[k]->geo, window_work(ctxs[k]));
+        items += 2 * (size_t)((ctxs[k]->g.particle_capacity + kMinChunk - 1) / kMinChunk);
+        items += (size_t)sort_blocks(ctxs[k]->geo) + 1;
     }
-    // each particle list holds at most max(resident blocks, simulations) items; resident
-    // blocks of 256 threads are at most 8 per SM
-    const size_t per_list = (size_t)(8 * device_sms() > n ? 8 * device_sms() : n);
-    return items + 3 * per_list;
+    return items;
 }
 }  // namespace
 
@@ -861,111 +869,157 @@ struct lpic_batch {
     std::vector<lpic_ctx *> ctx;
     lpic_precision prec = LPIC_FP64;
     cudaStream_t st = nullptr;
-    char *dbuf = nullptr;
-    size_t items_off = 0, items_cap = 0;   // int4 slots after the views
+    int *due = nullptr;                     // caller's device buffer: sort flags, then items
+    int4 *items = nullptr;
+    size_t items_cap = 0;
     cudaEvent_t ev = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> aux;          // branches of packs 1.. in the graph
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};   // one step; one step and the sorts
     std::vector<char> active_key;
-    int count[kBatchLists] = {};
-    size_t start[kBatchLists] = {};
-    int per_replay = 0;                     // fused launches per graph replay
-    long long launches = 0;                 // kernels enqueued by the batch (fused + per sim)
-    std::vector<int4> host_items;
+    std::vector<int> order;                 // context index of each flag (pack order)
+    int chunk = kDefaultChunk;              // particle slots per work item
+    int packs = 0;                          // packs requested (0: as few as the views allow)
+    int per_replay[2] = {0, 0};             // kernels per graph replay
+    long long launches = 0;                 // kernels enqueued by the batch (fused + relocation)
     std::string err;
 };
 
 namespace {
-void batch_release(lpic_batch *b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->ev) cudaEventDestroy(b->ev);
+void drop_graphs(lpic_batch *b) {
+    for (auto &e : b->exec)
+        if (e) { cudaGraphExecDestroy(e); e = nullptr; }
 }
 
-// Work lists of the active simulations.  Particle lists split each simulation's slots into
-// virtual blocks in proportion to its capacity, at most one item per resident block in all
-// (so that one wave covers the list and no block takes two items while others idle).
-template <class R> void plan_items(lpic_batch *b, const std::vector<char> &active) {
-    const int n = (int)b->ctx.size();
-    std::vector<int4> L[kBatchLists];
-    int nact = 0;
-    long long total = 0;
-    for (int k = 0; k < n; k++)
-        if (active[k]) {
-            nact++;
-            total += b->ctx[k]->g.particle_capacity;
-        }
-    const int gA = particle_multi_slots<R>(0, false);
-    for (int k = 0; k < n; k++) {
-        if (!active[k]) continue;
-        const lpic_ctx *c = b->ctx[k];
-        const int grid_list[3] = {0, 2, 5};
-        for (int ph = 0; ph < 3; ph++) {
-            int tx, ty;
-            grid_tiles(c->geo, ph, tx, ty);
-            for (int by = 0; by < ty; by++)
-                for (int bx = 0; bx < tx; bx++)
-                    L[grid_list[ph]].push_back(make_int4(k, bx, by, ph == 1 && bx == tx - 1 ? 1 : 0));
-        }
-        const long long cap = c->g.particle_capacity;
-        if (cap > 0) {
-            const bool dq = c->ph.track_dq != 0;
-            const int lists[2] = {1, dq ? 4 : 3};
-            const int slots[2] = {gA, particle_multi_slots<R>(1, dq)};
-            for (int q = 0; q < 2; q++) {
-                const long long room = slots[q] > nact ? slots[q] - nact : 1;
-                long long per = (total + room - 1) / room;
-                if (per < 256) per = 256;
-                const int nvb = (int)((cap + per - 1) / per);
-                for (int v = 0; v < nvb; v++) L[lists[q]].push_back(make_int4(k, v, nvb, 0));
-            }
-        }
-        const int parts = window_parts(c->geo, window_work(c));
-        for (int v = 0; v < parts; v++) L[6].push_back(make_int4(k, v, parts, 0));
-    }
-    b->host_items.clear();
-    for (int q = 0; q < kBatchLists; q++) {
-        b->start[q] = b->host_items.size();
-        b->count[q] = (int)L[q].size();
-        b->host_items.insert(b->host_items.end(), L[q].begin(), L[q].end());
-    }
+void batch_release(lpic_batch *b) {
+    drop_graphs(b);
+    if (b->ev) cudaEventDestroy(b->ev);
+    for (auto s : b->aux) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
 }
 
 template <class R> SimDev<R> &view_of(lpic_ctx *c);
 template <> SimDev<double> &view_of<double>(lpic_ctx *c) { return c->sd; }
 template <> SimDev<float> &view_of<float>(lpic_ctx *c) { return c->sf; }
 
-// Upload the views and the work lists, then record one step of the active set.
+// Work lists of one pack (sims: context indices of its simulations, pack slot = position).
+// Particle lists cut each simulation's slots [0, capacity) into items of b->chunk slots;
+// items are interleaved across simulations (all first items, then all second items, ...)
+// so that the items past a simulation's live slots, which end at once, spread over the
+// blocks instead of piling onto a few.
+void plan_pack(const lpic_batch *b, const std::vector<int> &sims, std::vector<int4> L[kBatchLists]) {
+    const int nact = (int)sims.size();
+    int most = 0;
+    for (int slot = 0; slot < nact; slot++) {
+        const lpic_ctx *c = b->ctx[sims[slot]];
+        const int grid_list[3] = {BL_PREPASS, BL_ENVELOPE, BL_AMPERE};
+        for (int ph = 0; ph < 3; ph++) {
+            int tx, ty;
+            grid_tiles(c->geo, ph, tx, ty);
+            for (int by = 0; by < ty; by++)
+                for (int bx = 0; bx < tx; bx++)
+                    L[grid_list[ph]].push_back(make_int4(slot, bx, by, ph == 1 && bx == tx - 1 ? 1 : 0));
+        }
+        const int parts = window_parts(c->geo, window_work(c));
+        for (int v = 0; v < parts; v++) L[BL_WINDOW].push_back(make_int4(slot, v, parts, 0));
+        const int nb = sort_blocks(c->geo);
+        for (int v = 0; v < nb; v++) L[BL_SORTBLK].push_back(make_int4(slot, v, 0, 0));
+        L[BL_SIMS].push_back(make_int4(slot, 0, 0, 0));
+        const long long ni = (c->g.particle_capacity + b->chunk - 1) / b->chunk;
+        if (ni > most) most = (int)ni;
+    }
+    for (int v = 0; v < most; v++)
+        for (int slot = 0; slot < nact; slot++) {
+            const lpic_ctx *c = b->ctx[sims[slot]];
+            if ((long long)v * b->chunk >= c->g.particle_capacity) continue;
+            const int4 it = make_int4(slot, v, 0, b->chunk);
+            L[BL_SLOTS].push_back(it);
+            L[c->ph.track_dq ? BL_PASSB_DQ : BL_PASSB].push_back(it);
+        }
+}
+
+// Upload the work lists, then record one step of the active set, without and with the
+// sorts (the sort launches act on the simulations whose flag is set before the replay).
 template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    plan_items<R>(b, active);
-    if (b->host_items.size() > b->items_cap) { b->err = "batch: work lists exceed the buffer"; return LPIC_EBUFSIZE; }
-    const int n = (int)b->ctx.size();
-    std::vector<SimDev<R>> views(n);
-    for (int k = 0; k < n; k++) views[k] = view_of<R>(b->ctx[k]);
-    const SimDev<R> *sims = (const SimDev<R> *)b->dbuf;
-    const int4 *items = (const int4 *)(b->dbuf + b->items_off);
-    // pageable sources: each copy returns once its source has been staged
-    cudaError_t e = cudaMemcpyAsync(b->dbuf, views.data(), n * sizeof(SimDev<R>), cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess && !b->host_items.empty())
-        e = cudaMemcpyAsync(b->dbuf + b->items_off, b->host_items.data(), b->host_items.size() * sizeof(int4),
-                            cudaMemcpyHostToDevice, b->st);
+    drop_graphs(b);
+    std::vector<int> act;
+    for (size_t k = 0; k < b->ctx.size(); k++)
+        if (active[k]) act.push_back((int)k);
+    int npk = pack_count((int)act.size());
+    if (b->packs > npk) npk = b->packs < (int)act.size() ? b->packs : (int)act.size();
+    if (npk < 1) npk = 1;
+    // packs of near-equal size
+    std::vector<std::vector<int>> packs(npk);
+    for (size_t q = 0; q < act.size(); q++) packs[q * npk / act.size()].push_back(act[q]);
+    std::vector<int4> host;
+    std::vector<std::array<size_t, kBatchLists>> start(npk);
+    std::vector<std::array<int, kBatchLists>> count(npk);
+    std::vector<int> flag0(npk);
+    b->order.clear();
+    for (int p = 0; p < npk; p++) {
+        std::vector<int4> L[kBatchLists];
+        plan_pack(b, packs[p], L);
+        for (int q = 0; q < kBatchLists; q++) {
+            start[p][q] = host.size();
+            count[p][q] = (int)L[q].size();
+            host.insert(host.end(), L[q].begin(), L[q].end());
+        }
+        flag0[p] = (int)b->order.size();
+        b->order.insert(b->order.end(), packs[p].begin(), packs[p].end());
+    }
+    if (host.size() > b->items_cap) { b->err = "batch: work lists exceed the buffer"; return LPIC_EBUFSIZE; }
+    // a pageable source: the copy returns once the source has been staged
+    cudaError_t e = host.empty() ? cudaSuccess
+                                 : cudaMemcpyAsync(b->items, host.data(), host.size() * sizeof(int4),
+                                                   cudaMemcpyHostToDevice, b->st);
     if (e != cudaSuccess) { b->err = std::string("batch upload: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
-    int nl = 0;
-    auto it = [&](int q) { nl += b->count[q] > 0; return items + b->start[q]; };
-    launch_grid_multi<R>(0, sims, it(0), b->count[0], b->st);
-    launch_particles_multi<R>(0, false, sims, it(1), b->count[1], b->st);
-    launch_grid_multi<R>(1, sims, it(2), b->count[2], b->st);
-    launch_particles_multi<R>(1, false, sims, it(3), b->count[3], b->st);
-    launch_particles_multi<R>(1, true, sims, it(4), b->count[4], b->st);
-    launch_grid_multi<R>(2, sims, it(5), b->count[5], b->st);
-    launch_window_multi<R>(sims, it(6), b->count[6], b->st);
-    e = cudaStreamEndCapture(b->st, &graph);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
-    b->per_replay = nl;
+    while ((int)b->aux.size() < npk - 1) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t j = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e != cudaSuccess) { b->err = std::string("batch: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
+        b->aux.push_back(s);
+        b->join.push_back(j);
+    }
+    std::unique_ptr<SimPack<R>> pk(new SimPack<R>());
+    for (int g = 0; g < 2; g++) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        cudaEventRecord(b->ev, b->st);
+        int nl = 0;
+        for (int p = 0; p < npk; p++) {
+            cudaStream_t st = p == 0 ? b->st : b->aux[p - 1];
+            if (p > 0) cudaStreamWaitEvent(st, b->ev, 0);
+            for (size_t q = 0; q < packs[p].size(); q++) pk->v[q] = view_of<R>(b->ctx[packs[p][q]]);
+            const auto &cn = count[p];
+            auto it = [&](int q) { return (const int4 *)(b->items + start[p][q]); };
+            for (int q : {BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_AMPERE, BL_WINDOW})
+                nl += cn[q] > 0;
+            launch_grid_multi<R>(0, *pk, it(BL_PREPASS), cn[BL_PREPASS], st);
+            launch_particles_multi<R>(0, false, *pk, it(BL_SLOTS), cn[BL_SLOTS], st);
+            launch_grid_multi<R>(1, *pk, it(BL_ENVELOPE), cn[BL_ENVELOPE], st);
+            launch_particles_multi<R>(1, false, *pk, it(BL_PASSB), cn[BL_PASSB], st);
+            launch_particles_multi<R>(1, true, *pk, it(BL_PASSB_DQ), cn[BL_PASSB_DQ], st);
+            launch_grid_multi<R>(2, *pk, it(BL_AMPERE), cn[BL_AMPERE], st);
+            launch_window_multi<R>(*pk, it(BL_WINDOW), cn[BL_WINDOW], st);
+            if (g == 1 && cn[BL_SIMS] > 0) {
+                launch_sort_multi<R>(*pk, b->due + flag0[p], it(BL_SORTBLK), cn[BL_SORTBLK], it(BL_SLOTS),
+                                     cn[BL_SLOTS], it(BL_SIMS), cn[BL_SIMS], st);
+                nl += kSortLaunchesMulti - (cn[BL_SORTBLK] > 0 ? 0 : 3) - (cn[BL_SLOTS] > 0 ? 0 : 2);
+            }
+            if (p > 0) {
+                cudaEventRecord(b->join[p - 1], st);
+                cudaStreamWaitEvent(b->st, b->join[p - 1], 0);
+            }
+        }
+        e = cudaStreamEndCapture(b->st, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[g], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
+        b->per_replay[g] = nl;
+    }
     b->active_key = active;
     return LPIC_OK;
 }
@@ -977,8 +1031,7 @@ size_t lpic_batch_required_bytes(lpic_ctx *const *ctxs, int n) {
     if (!ctxs || n <= 0) return 0;
     for (int k = 0; k < n; k++)
         if (!ctxs[k] || ctxs[k]->prec != ctxs[0]->prec) return 0;
-    return round_up((size_t)n * sim_view_bytes(ctxs[0]->prec), kBatchAlign) +
-           batch_items_bound(ctxs, n) * sizeof(int4);
+    return flags_bytes(n) + batch_items_bound(ctxs, n) * sizeof(int4);
 }
 
 lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, void *device_buf,
@@ -993,7 +1046,7 @@ lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, vo
         for (int q = k + 1; q < n; q++)
             if (ctxs[k] == ctxs[q]) { g_thread_err = "batch: a context appears twice"; return LPIC_EINVAL; }
     const size_t need = lpic_batch_required_bytes(ctxs, n);
-    if (!device_buf || ((uintptr_t)device_buf % kBatchAlign) != 0) {
+    if (!device_buf || ((uintptr_t)device_buf % 256) != 0) {
         g_thread_err = "batch: device_buf must be non-NULL and 256-byte aligned";
         return LPIC_EINVAL;
     }
@@ -1002,9 +1055,9 @@ lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, vo
     b->ctx.assign(ctxs, ctxs + n);
     b->prec = ctxs[0]->prec;
     b->st = (cudaStream_t)cuda_stream;
-    b->dbuf = (char *)device_buf;
-    b->items_off = round_up((size_t)n * sim_view_bytes(b->prec), kBatchAlign);
-    b->items_cap = (buf_bytes - b->items_off) / sizeof(int4);
+    b->due = (int *)device_buf;
+    b->items = (int4 *)((char *)device_buf + flags_bytes(n));
+    b->items_cap = (buf_bytes - flags_bytes(n)) / sizeof(int4);
     cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         g_thread_err = std::string("batch: ") + cudaGetErrorString(e);
@@ -1018,45 +1071,69 @@ lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, vo
 
 lpic_status lpic_batch_step(lpic_batch *b, const int *steps) {
     if (!b || !steps) return LPIC_EINVAL;
+    const size_t n = b->ctx.size();
     int maxs = 0;
-    for (size_t k = 0; k < b->ctx.size(); k++) {
+    for (size_t k = 0; k < n; k++) {
         if (steps[k] < 0) { b->err = "batch: negative step count"; return LPIC_EINVAL; }
         if (steps[k] > maxs) maxs = steps[k];
     }
     if (maxs == 0) return LPIC_OK;
     // order after earlier work on the contexts' own streams
-    for (size_t k = 0; k < b->ctx.size(); k++) {
+    for (size_t k = 0; k < n; k++) {
         cudaEventRecord(b->ev, b->ctx[k]->st);
         cudaStreamWaitEvent(b->st, b->ev, 0);
     }
-    std::vector<char> active(b->ctx.size());
+    std::vector<char> active(n), sort(n);
+    std::vector<int> flags;
     for (int t = 0; t < maxs; t++) {
-        for (size_t k = 0; k < b->ctx.size(); k++) active[k] = steps[k] > t;
-        for (size_t k = 0; k < b->ctx.size(); k++)
+        for (size_t k = 0; k < n; k++) active[k] = steps[k] > t;
+        for (size_t k = 0; k < n; k++)
             if (active[k]) {
                 const long long r0 = b->ctx[k]->launches[F_RELOCATE];
                 pre_step(b->ctx[k], b->st);
                 b->launches += b->ctx[k]->launches[F_RELOCATE] - r0;
             }
-        if (!b->exec || active != b->active_key) {
+        if (!b->exec[0] || active != b->active_key) {
             lpic_status s = b->prec == LPIC_FP64 ? batch_capture<double>(b, active) : batch_capture<float>(b, active);
             if (s != LPIC_OK) return s;
         }
-        cudaError_t e = cudaGraphLaunch(b->exec, b->st);
+        bool any = false;
+        for (size_t k = 0; k < n; k++) {
+            sort[k] = active[k] && advance_mirror(b->ctx[k]);
+            any = any || sort[k];
+        }
+        if (any) {
+            flags.resize(b->order.size());
+            for (size_t q = 0; q < b->order.size(); q++) flags[q] = sort[b->order[q]] ? 1 : 0;
+            // a pageable source: the copy returns once the source has been staged
+            cudaError_t e = cudaMemcpyAsync(b->due, flags.data(), flags.size() * sizeof(int),
+                                            cudaMemcpyHostToDevice, b->st);
+            if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        }
+        cudaError_t e = cudaGraphLaunch(b->exec[any ? 1 : 0], b->st);
         if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
-        b->launches += b->per_replay;
-        for (size_t k = 0; k < b->ctx.size(); k++)
-            if (active[k]) {
-                const long long s0 = b->ctx[k]->launches[F_SORT];
-                post_step(b->ctx[k], b->st);
-                b->launches += b->ctx[k]->launches[F_SORT] - s0;
-            }
+        b->launches += b->per_replay[any ? 1 : 0];
     }
     // later calls on a context's own stream come after this batch step
     cudaEventRecord(b->ev, b->st);
-    for (size_t k = 0; k < b->ctx.size(); k++) cudaStreamWaitEvent(b->ctx[k]->st, b->ev, 0);
+    for (size_t k = 0; k < n; k++) cudaStreamWaitEvent(b->ctx[k]->st, b->ev, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+    return LPIC_OK;
+}
+
+lpic_status lpic_batch_set_tuning(lpic_batch *b, int32_t particles_per_item, int32_t packs) {
+    if (!b) return LPIC_EINVAL;
+    if (particles_per_item < kMinChunk || particles_per_item > kMaxChunk || particles_per_item % 256) {
+        b->err = "batch: particles_per_item must be a multiple of 256 in [1024, 1048576]";
+        return LPIC_EINVAL;
+    }
+    if (packs < 0) { b->err = "batch: packs must be >= 0"; return LPIC_EINVAL; }
+    if (particles_per_item != b->chunk || packs != b->packs) {
+        b->chunk = particles_per_item;
+        b->packs = packs;
+        drop_graphs(b);   // re-planned at the next step
+    }
     return LPIC_OK;
 }
 

@@ -195,24 +195,24 @@ template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, blo
 
 // Fused forms over a batch: each block walks work items {simulation, bx, by, flag}.
 template <class R>
-__global__ void __launch_bounds__(BX * BY) k_prepass_multi(const SimDev<R> *sims, const int4 *items, int n) {
+__global__ void __launch_bounds__(BX * BY) k_prepass_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        prepass_tile<R>(sims[it.x], it.y, it.z);
+        prepass_tile<R>(pk.v[it.x], it.y, it.z);
     }
 }
 template <class R>
-__global__ void __launch_bounds__(BX * BY) k_envelope_multi(const SimDev<R> *sims, const int4 *items, int n) {
+__global__ void __launch_bounds__(BX * BY) k_envelope_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        envelope_tile<R>(sims[it.x], it.y, it.z, it.w != 0);
+        envelope_tile<R>(pk.v[it.x], it.y, it.z, it.w != 0);
     }
 }
 template <class R>
-__global__ void __launch_bounds__(BX * BY) k_ampere_multi(const SimDev<R> *sims, const int4 *items, int n) {
+__global__ void __launch_bounds__(BX * BY) k_ampere_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        ampere_tile<R>(sims[it.x], it.y, it.z);
+        ampere_tile<R>(pk.v[it.x], it.y, it.z);
     }
 }
 
@@ -307,24 +307,24 @@ template <class K> int resident(K *kernel, int threads) {
 }
 
 template <class R>
-void launch_grid_multi(int phase, const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st) {
+void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st) {
     if (n <= 0) return;
     static int res[3] = {0, 0, 0};
     const dim3 blk(BX, BY);
     if (phase == 0) {
         if (!res[0]) res[0] = resident(k_prepass_multi<R>, BX * BY);
-        k_prepass_multi<R><<<n < res[0] ? n : res[0], blk, 0, st>>>(sims, items, n);
+        k_prepass_multi<R><<<n < res[0] ? n : res[0], blk, 0, st>>>(pk, items, n);
     } else if (phase == 1) {
         if (!res[1]) res[1] = resident(k_envelope_multi<R>, BX * BY);
-        k_envelope_multi<R><<<n < res[1] ? n : res[1], blk, 0, st>>>(sims, items, n);
+        k_envelope_multi<R><<<n < res[1] ? n : res[1], blk, 0, st>>>(pk, items, n);
     } else {
         if (!res[2]) res[2] = resident(k_ampere_multi<R>, BX * BY);
-        k_ampere_multi<R><<<n < res[2] ? n : res[2], blk, 0, st>>>(sims, items, n);
+        k_ampere_multi<R><<<n < res[2] ? n : res[2], blk, 0, st>>>(pk, items, n);
     }
 }
 
 #define INST(R)                                                                              \
-    template void launch_grid_multi<R>(int, const SimDev<R> *, const int4 *, int, cudaStream_t); \
+    template void launch_grid_multi<R>(int, const SimPack<R> &, const int4 *, int, cudaStream_t); \
     template void launch_prepass<R>(const SimDev<R> &, cudaStream_t);                        \
     template void launch_envelope<R>(const SimDev<R> &, cudaStream_t);                       \
     template void launch_ampere<R>(const SimDev<R> &, cudaStream_t);                         \

@@ -105,6 +105,11 @@ template <class R> struct Kc {
     const R *tab;   // NTAB x P row tables
 };
 
+// Scratch of the counting sort: key per slot, ncell + 2 counters, scan block sums.
+struct SortBufs {
+    int *key, *count, *blocksum;
+};
+
 template <class R> struct SimDev {
     Geo geo;
     Phys ph;
@@ -112,6 +117,7 @@ template <class R> struct SimDev {
     Desc *d;
     Fields<R> f;
     Parts<R> p[2];   // p[d->pbuf] in use; the counting sort scatters into the other
+    SortBufs sb;
 };
 
 // ---- shared device helpers -------------------------------------------------------------
@@ -216,18 +222,34 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
 template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
 
 // ---- fused batch forms: one launch per phase over work items {sim, a, b, c} -------------
+// The views of the simulations of one fused launch travel by value in the kernel's
+// parameter space (a __grid_constant__ pack, read through the constant cache like a single
+// simulation's view, so the bodies keep the register budget of the single kernels).
+// 52 views of at most 592 bytes plus the other arguments fit the 32,764-byte limit.
+constexpr int kPackMax = 52;
+template <class R> struct SimPack { SimDev<R> v[kPackMax]; };
+static_assert(sizeof(SimPack<double>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764 &&
+                  sizeof(SimPack<float>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764,
+              "a pack of views must fit the kernel parameter space");
 // grid phases 0 prepass, 1 envelope (c = axis tile), 2 ampere: items {sim, bx, by, c}
 void grid_tiles(const Geo &g, int phase, int &tx, int &ty);
 template <class R>
-void launch_grid_multi(int phase, const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st);
-// particle phases (0 pass A, 1 pass B): items {sim, virtual block, virtual blocks of sim, 0}
+void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);
+// particle phases (0 pass A, 1 pass B): items {sim, item, 0, slots per item}, item covering
+// slots [item * size, (item + 1) * size) clipped to the live slots
 template <class R>
-void launch_particles_multi(int phase, bool dq, const SimDev<R> *sims, const int4 *items, int n,
+void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4 *items, int n,
                             cudaStream_t st);
-// blocks of the fused particle kernel resident on the device at once (phase 0: pass A)
-template <class R> int particle_multi_slots(int phase, bool dq);
 // window: items {sim, part, parts of sim, 0}
-template <class R> void launch_window_multi(const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st);
+template <class R> void launch_window_multi(const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);
+// counting sort of the simulations with due[slot] != 0, seven launches: clear, count, scan
+// blocks, scan top, scan add, scatter, finish.  blocks: items {sim, block of 4096 counters,
+// 0, 0} (clear and scans); slots: particle items as for the passes; sims: {sim, 0, 0, 0}.
+template <class R>
+void launch_sort_multi(const SimPack<R> &pk, const int *due, const int4 *blocks, int nblocks,
+                       const int4 *slots, int nslots, const int4 *sims, int nsims, cudaStream_t st);
+constexpr int kSortLaunchesMulti = 7;
+__host__ __device__ inline int sort_blocks(const Geo &g) { return (g.nx * g.nr + 1 + 4095) / 4096; }
 constexpr int kWindowThreads = 64;
 int window_parts(const Geo &g, int work);   // blocks of the single-simulation window launch
 

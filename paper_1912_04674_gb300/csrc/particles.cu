@@ -206,7 +206,17 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
 //   chi += q^2 w S/(gt V_chi),  F = qE - gradPhi/(2 gt),  Boris rotation with g- .
 // Every lane computes (a hole or a lane past the end works on harmless zeros or stale
 // values) and the results are masked, so the loop body has no data-dependent branch.
-template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &S, int vb, int nvb) {
+// Slots of block vb of nvb (single launch: near-equal contiguous chunks of the live slots),
+// or of item vb of a fixed size csize > 0 (fused launches), clipped to the live slots.
+__device__ __forceinline__ int2 slot_range(int np, int vb, int nvb, int csize) {
+    int chunk = csize;
+    if (chunk <= 0) chunk = ((np + nvb - 1) / nvb + TPB - 1) / TPB * TPB;
+    const long long b = (long long)vb * chunk;
+    const int begin = b < np ? (int)b : np;
+    return make_int2(begin, min(begin + chunk, np));
+}
+
+template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &S, int vb, int nvb, int csize) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
@@ -216,8 +226,8 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
     const R q = (R)-1;
     // each block walks one contiguous chunk of slots, so that its successive iterations
     // gather from neighbouring cells (field lines stay in L1)
-    const int chunk = ((np + nvb - 1) / nvb + TPB - 1) / TPB * TPB;
-    const int begin = vb * chunk, end = min(begin + chunk, np);
+    const int2 rg = slot_range(np, vb, nvb, csize);
+    const int begin = rg.x, end = rg.y;
     int k = begin + threadIdx.x;
     PReg<R> cur = load_particle<R>(P, k, end);
     for (int base = begin; base < end; base += TPB, k += TPB) {
@@ -287,7 +297,7 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
 }
 
 template <class R> __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a(SimDev<R> S) {
-    pass_a_body<R>(S, blockIdx.x, gridDim.x);
+    pass_a_body<R>(S, blockIdx.x, gridDim.x, 0);
 }
 
 // Linear shape of a particle in cell i0 with fraction f, on the nodes base, base+1, base+2
@@ -366,7 +376,7 @@ __device__ __forceinline__ void drain_queue(const SimDev<R> &S, int off, CrossQu
 // cent) are queued per warp in shared memory and take the 3x3 general form 32 at a time, so
 // that their slow path runs on full warps.  Particles leaving the next step's window (x < 0,
 // x >= Nx dx) or reaching r >= r_max are marked dead after their deposit.
-template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const SimDev<R> &S, int vb, int nvb) {
+template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const SimDev<R> &S, int vb, int nvb, int csize) {
     __shared__ CrossQueue<R> Q;
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
@@ -380,8 +390,8 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     int queued = 0;   // same value on every lane of the warp
     // each block walks one contiguous chunk of slots (see pass A)
-    const int chunk = ((np + nvb - 1) / nvb + TPB - 1) / TPB * TPB;
-    const int begin = vb * chunk, end = min(begin + chunk, np);
+    const int2 rg = slot_range(np, vb, nvb, csize);
+    const int begin = rg.x, end = rg.y;
     int k = begin + threadIdx.x;
     PReg<R> cur = load_particle<R>(P, k, end);
     for (int base = begin; base < end; base += TPB, k += TPB) {
@@ -478,23 +488,23 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
 
 template <class R, bool DQ>
 __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b(SimDev<R> S) {
-    pass_b_body<R, DQ>(S, blockIdx.x, gridDim.x);
+    pass_b_body<R, DQ>(S, blockIdx.x, gridDim.x, 0);
 }
 
-// Fused forms over a batch: each block walks work items {simulation, virtual block, virtual
-// blocks of that simulation}.
+// Fused forms over a batch: each block walks work items {simulation, item, 0, slots per
+// item}.
 template <class R>
-__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a_multi(const SimDev<R> *sims, const int4 *items, int n) {
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        pass_a_body<R>(sims[it.x], it.y, it.z);
+        pass_a_body<R>(pk.v[it.x], it.y, it.z, it.w);
     }
 }
 template <class R, bool DQ>
-__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b_multi(const SimDev<R> *sims, const int4 *items, int n) {
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        pass_b_body<R, DQ>(sims[it.x], it.y, it.z);
+        pass_b_body<R, DQ>(pk.v[it.x], it.y, it.z, it.w);
     }
 }
 
@@ -557,31 +567,25 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
     if (total > 0) k_load_columns<R><<<pgrid(total), TPB, 0, st>>>(S, d_colbase, ncols, total);
 }
 
-template <class R> int particle_multi_slots(int phase, bool dq) {
-    if (phase == 0) return resident_blocks(k_pass_a_multi<R>);
-    return dq ? resident_blocks(k_pass_b_multi<R, true>) : resident_blocks(k_pass_b_multi<R, false>);
-}
-
 template <class R>
-void launch_particles_multi(int phase, bool dq, const SimDev<R> *sims, const int4 *items, int n,
+void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4 *items, int n,
                             cudaStream_t st) {
     if (n <= 0) return;
     int g;
     if (phase == 0) {
         g = resident_blocks(k_pass_a_multi<R>);
-        k_pass_a_multi<R><<<n < g ? n : g, TPB, 0, st>>>(sims, items, n);
+        k_pass_a_multi<R><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
     } else if (dq) {
         g = resident_blocks(k_pass_b_multi<R, true>);
-        k_pass_b_multi<R, true><<<n < g ? n : g, TPB, 0, st>>>(sims, items, n);
+        k_pass_b_multi<R, true><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
     } else {
         g = resident_blocks(k_pass_b_multi<R, false>);
-        k_pass_b_multi<R, false><<<n < g ? n : g, TPB, 0, st>>>(sims, items, n);
+        k_pass_b_multi<R, false><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
     }
 }
 
 #define INST(R)                                                                             \
-    template int particle_multi_slots<R>(int, bool);                                        \
-    template void launch_particles_multi<R>(int, bool, const SimDev<R> *, const int4 *, int, \
+    template void launch_particles_multi<R>(int, bool, const SimPack<R> &, const int4 *, int, \
                                             cudaStream_t);                                  \
     template void launch_pass_a<R>(const SimDev<R> &, int, cudaStream_t);                   \
     template void launch_pass_b<R>(const SimDev<R> &, int, cudaStream_t);                   \

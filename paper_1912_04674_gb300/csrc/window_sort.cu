@@ -80,22 +80,23 @@ template <class R> __device__ __forceinline__ void window_body(const SimDev<R> &
 template <class R> __global__ void k_window(SimDev<R> S) { window_body<R>(S, blockIdx.x, gridDim.x); }
 
 // Fused form over a batch: items {simulation, part, parts of that simulation}.
-template <class R> __global__ void k_window_multi(const SimDev<R> *sims, const int4 *items, int n) {
+template <class R> __global__ void k_window_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        window_body<R>(sims[it.x], it.y, it.z);
+        window_body<R>(pk.v[it.x], it.y, it.z);
         __syncthreads();   // the body's block-level bookkeeping must not overlap the next item
     }
 }
 
 // ---- counting sort by window cell (x-major, r fastest, like the grid) -------------------
-template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *count) {
+// Cell key of slots k = k0, k0 + stride, ... < k1 and the per-cell counts.
+template <class R>
+__device__ __forceinline__ void sort_count_span(const SimDev<R> &S, int *key, int *count, int k0, int k1, int stride) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
-    const int np = S.d->np;
     const long long s = S.d->shift;
     const int ncell = S.geo.nx * S.geo.nr;
     const R idr = S.k.idr;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+    for (int k = k0; k < k1; k += stride) {
         const int ix = P.ix[k];
         int c;
         if (ix == kDead) {
@@ -113,6 +114,10 @@ template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *coun
         const unsigned grp = __match_any_sync(__activemask(), c);
         if ((int)(__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicAdd(count + c, __popc(grp));
     }
+}
+
+template <class R> __global__ void k_sort_count(SimDev<R> S, int *key, int *count) {
+    sort_count_span<R>(S, key, count, blockIdx.x * blockDim.x + threadIdx.x, S.d->np, gridDim.x * blockDim.x);
 }
 
 // Exclusive scan of count[0..n) in place, three phases over blocks of 4096 items.
@@ -144,9 +149,9 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *sh) {
     return before + x - v;
 }
 
-__global__ void k_scan_blocks(int *data, int n, int *blocksum) {
+__device__ __forceinline__ void scan_blocks_body(int *data, int n, int *blocksum, int b) {
     __shared__ int sh[40];
-    const int base = blockIdx.x * SB * SI + threadIdx.x * SI;
+    const int base = b * SB * SI + threadIdx.x * SI;
     int v[SI], tsum = 0;
 #pragma unroll
     for (int q = 0; q < SI; q++) {
@@ -159,10 +164,11 @@ __global__ void k_scan_blocks(int *data, int n, int *blocksum) {
         if (base + q < n) data[base + q] = ex;
         ex += v[q];
     }
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = sh[32];
+    if (threadIdx.x == 0) blocksum[b] = sh[32];
+    __syncthreads();   // sh is reused by the next call of this block
 }
 
-__global__ void k_scan_top(int *blocksum, int nb) {  // one block, nb <= SB*SI
+__device__ __forceinline__ void scan_top_body(int *blocksum, int nb) {  // nb <= SB*SI
     __shared__ int sh[40];
     const int base = threadIdx.x * SI;
     int v[SI], tsum = 0;
@@ -177,23 +183,29 @@ __global__ void k_scan_top(int *blocksum, int nb) {  // one block, nb <= SB*SI
         if (base + q < nb) blocksum[base + q] = ex;
         ex += v[q];
     }
+    __syncthreads();
 }
 
-__global__ void k_scan_add(int *data, int n, const int *blocksum) {
-    const int b = blockIdx.x, add = blocksum[b];
+__device__ __forceinline__ void scan_add_body(int *data, int n, const int *blocksum, int b) {
+    const int add = blocksum[b];
     const int base = b * SB * SI + threadIdx.x * SI;
 #pragma unroll
     for (int q = 0; q < SI; q++)
         if (base + q < n) data[base + q] += add;
 }
 
+__global__ void k_scan_blocks(int *data, int n, int *blocksum) { scan_blocks_body(data, n, blocksum, blockIdx.x); }
+__global__ void k_scan_top(int *blocksum, int nb) { scan_top_body(blocksum, nb); }
+__global__ void k_scan_add(int *data, int n, const int *blocksum) { scan_add_body(data, n, blocksum, blockIdx.x); }
+
+// Scatter of slots k = k0, k0 + stride, ... < k1 to their cells' cursors (dead slots drop).
 template <class R>
-__global__ void k_sort_scatter(SimDev<R> S, const int *key, int *cursor) {
+__device__ __forceinline__ void sort_scatter_span(const SimDev<R> &S, const int *key, int *cursor, int k0, int k1,
+                                                  int stride) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Parts<R> out = S.d->pbuf ? S.p[0] : S.p[1];
-    const int np = S.d->np;
     const int ncell = S.geo.nx * S.geo.nr;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+    for (int k = k0; k < k1; k += stride) {
         const int c = key[k];
         // one atomic per group of lanes with the same cell; ranks within the group by lane
         const unsigned grp = __match_any_sync(__activemask(), c);
@@ -215,13 +227,98 @@ __global__ void k_sort_scatter(SimDev<R> S, const int *key, int *cursor) {
     }
 }
 
+template <class R>
+__global__ void k_sort_scatter(SimDev<R> S, const int *key, int *cursor) {
+    sort_scatter_span<R>(S, key, cursor, blockIdx.x * blockDim.x + threadIdx.x, S.d->np, gridDim.x * blockDim.x);
+}
+
 // After the scatter cursor[c] = end of cell c, so cursor[ncell-1] is the alive count.
-template <class R> __global__ void k_sort_finish(SimDev<R> S, const int *cursor) {
+template <class R> __device__ __forceinline__ void sort_finish_body(const SimDev<R> &S, const int *cursor) {
     const int ncell = S.geo.nx * S.geo.nr;
     const int alive = ncell > 0 ? cursor[ncell - 1] : 0;
     S.d->np = alive;
     S.d->n_alive = alive;
     S.d->pbuf ^= 1;
+}
+template <class R> __global__ void k_sort_finish(SimDev<R> S, const int *cursor) { sort_finish_body<R>(S, cursor); }
+
+// ---- fused counting sort over a pack of simulations (those with due[slot] != 0) --------
+template <class R>
+__global__ void __launch_bounds__(SB) k_sort_clear_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                         const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;
+        const SimDev<R> &S = pk.v[it.x];
+        const int nc = S.geo.nx * S.geo.nr + 2;
+        const int base = it.y * SB * SI + threadIdx.x * SI;
+#pragma unroll
+        for (int q = 0; q < SI; q++)
+            if (base + q < nc) S.sb.count[base + q] = 0;
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(TPB) k_sort_count_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                          const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;
+        const SimDev<R> &S = pk.v[it.x];
+        const int np = S.d->np;
+        const long long b0 = (long long)it.y * it.w;
+        const int begin = b0 < np ? (int)b0 : np, end = min(begin + it.w, np);
+        sort_count_span<R>(S, S.sb.key, S.sb.count, begin + threadIdx.x, end, TPB);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(SB) k_scan_blocks_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                          const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;   // block-uniform: the whole block skips or takes the item
+        const SimDev<R> &S = pk.v[it.x];
+        scan_blocks_body(S.sb.count, S.geo.nx * S.geo.nr + 1, S.sb.blocksum, it.y);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(SB) k_scan_top_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                       const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;
+        const SimDev<R> &S = pk.v[it.x];
+        scan_top_body(S.sb.blocksum, sort_blocks(S.geo));
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(SB) k_scan_add_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                       const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;
+        const SimDev<R> &S = pk.v[it.x];
+        scan_add_body(S.sb.count, S.geo.nx * S.geo.nr + 1, S.sb.blocksum, it.y);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(TPB) k_sort_scatter_multi(const __grid_constant__ SimPack<R> pk, const int *due,
+                                                            const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        if (!due[it.x]) continue;
+        const SimDev<R> &S = pk.v[it.x];
+        const int np = S.d->np;
+        const long long b0 = (long long)it.y * it.w;
+        const int begin = b0 < np ? (int)b0 : np, end = min(begin + it.w, np);
+        sort_scatter_span<R>(S, S.sb.key, S.sb.count, begin + threadIdx.x, end, TPB);
+    }
+}
+template <class R>
+__global__ void k_sort_finish_multi(const __grid_constant__ SimPack<R> pk, const int *due, const int4 *items, int n) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    const int4 it = items[w];
+    if (due[it.x]) sort_finish_body<R>(pk.v[it.x], pk.v[it.x].sb.count);
 }
 
 inline int pgrid(int n) {
@@ -243,8 +340,8 @@ template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStr
     k_window<R><<<window_parts(S.geo, work), kWindowThreads, 0, st>>>(S);
 }
 
-template <class R> void launch_window_multi(const SimDev<R> *sims, const int4 *items, int n, cudaStream_t st) {
-    if (n > 0) k_window_multi<R><<<n < 152 * 8 ? n : 152 * 8, kWindowThreads, 0, st>>>(sims, items, n);
+template <class R> void launch_window_multi(const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st) {
+    if (n > 0) k_window_multi<R><<<n < 152 * 8 ? n : 152 * 8, kWindowThreads, 0, st>>>(pk, items, n);
 }
 
 // Exclusive scan of n <= SB*SI*SB*SI ints in place.
@@ -267,9 +364,26 @@ void launch_sort(const SimDev<R> &S, int np_upper, int *key, int *count, int *bl
     k_sort_finish<R><<<1, 1, 0, st>>>(S, count);
 }
 
+template <class R>
+void launch_sort_multi(const SimPack<R> &pk, const int *due, const int4 *blocks, int nblocks,
+                       const int4 *slots, int nslots, const int4 *sims, int nsims, cudaStream_t st) {
+    if (nsims <= 0) return;
+    const int gb = nblocks < 152 * 2 ? nblocks : 152 * 2;     // 1024-thread blocks, 2 per SM
+    const int gs = nslots < 152 * 8 ? nslots : 152 * 8;       // 256-thread blocks, 8 per SM
+    if (gb > 0) k_sort_clear_multi<R><<<gb, SB, 0, st>>>(pk, due, blocks, nblocks);
+    if (gs > 0) k_sort_count_multi<R><<<gs, TPB, 0, st>>>(pk, due, slots, nslots);
+    if (gb > 0) k_scan_blocks_multi<R><<<gb, SB, 0, st>>>(pk, due, blocks, nblocks);
+    k_scan_top_multi<R><<<nsims, SB, 0, st>>>(pk, due, sims, nsims);
+    if (gb > 0) k_scan_add_multi<R><<<gb, SB, 0, st>>>(pk, due, blocks, nblocks);
+    if (gs > 0) k_sort_scatter_multi<R><<<gs, TPB, 0, st>>>(pk, due, slots, nslots);
+    k_sort_finish_multi<R><<<(nsims + 63) / 64, 64, 0, st>>>(pk, due, sims, nsims);
+}
+
 #define INST(R)                                                                          \
+    template void launch_sort_multi<R>(const SimPack<R> &, const int *, const int4 *, int, \
+                                       const int4 *, int, const int4 *, int, cudaStream_t); \
     template void launch_window<R>(const SimDev<R> &, int, cudaStream_t);                \
-    template void launch_window_multi<R>(const SimDev<R> *, const int4 *, int, cudaStream_t); \
+    template void launch_window_multi<R>(const SimPack<R> &, const int4 *, int, cudaStream_t); \
     template void launch_sort<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t);
 INST(double)
 INST(float)

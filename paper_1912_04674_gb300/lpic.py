@@ -79,6 +79,7 @@ _SIGS = {
     "lpic_batch_required_bytes": (C.c_size_t, [C.POINTER(C.c_void_p), C.c_int]),
     "lpic_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpic_batch_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "lpic_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "lpic_batch_launches": (C.c_int64, [C.c_void_p]),
     "lpic_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lpic_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -220,6 +221,12 @@ def lpic_batch_step(batch, steps):
         raise LpicError(st, lpic_batch_last_error(batch))
 
 
+def lpic_batch_set_tuning(batch, particles_per_item: int, packs: int = 0):
+    st = lib().lpic_batch_set_tuning(batch, int(particles_per_item), int(packs))
+    if st != LPIC_OK:
+        raise LpicError(st, lpic_batch_last_error(batch))
+
+
 def lpic_batch_launches(batch) -> int:
     return int(lib().lpic_batch_launches(batch))
 
@@ -253,6 +260,9 @@ class Batch:
 
     def step(self, steps):
         lpic_batch_step(self.b, steps)
+
+    def set_tuning(self, particles_per_item: int, packs: int = 0):
+        lpic_batch_set_tuning(self.b, particles_per_item, packs)
 
     def launches(self) -> int:
         return lpic_batch_launches(self.b)

@@ -125,6 +125,10 @@ class ScanServer:
             self._batch = None
         if self.running:
             self._batch = L.Batch([r.sim for r in self.running], self.stream)
+            # a tuned work-item size if one was measured for this bucket (tuning itself
+            # would advance the jobs past their step counts, so the server never tunes)
+            total = sum(int(r.sim.gs.particle_capacity) for r in self.running)
+            self._batch.set_tuning(*autotune.batch_tuning_for(total, len(self.running), self.precision))
         self._batch_key = key
 
     def _admit(self, now: float):

@@ -45,15 +45,42 @@ def test_batch_matches_alone(precision, tol):
     b = L.Batch(mixed, torch.cuda.Stream())
     b.step([10, 10, 10])          # all three together
     b.step([20, 35, 10])          # uneven: later launches run fewer simulations
-    # one fused launch per phase (pass B of the untracked simulations only) per step, plus
-    # the per-simulation sorts every 5 steps
-    assert b.launches() == 6 * 45 + sum(n // 5 * 6 for n in steps)
+    # one fused launch per phase (pass B of the untracked simulations only) per step; the
+    # three simulations sort together every 5 steps in seven more fused launches
+    assert b.launches() == 6 * 45 + 7 * (45 // 5)
     b.close()
     for a, m, n in zip(alone, mixed, steps):
         assert m.counters()["step"] == n
         for f in ("ex", "er", "bt", "a", "chi", "jx"):
             assert rel_err(m.field(f), a.field(f)) < tol, (f, rel_err(m.field(f), a.field(f)))
         assert a.counters() == m.counters()
+
+
+def test_batch_larger_than_one_pack_matches_alone():
+    """More simulations than one launch's parameter pack holds: the batch splits them into
+    packs whose launch sequences run as parallel graph branches."""
+    import torch
+
+    from paper_1912_04674_gb300 import lpic as L
+    base = dataclasses.replace(C1, a0=0.5, L=6.0, n0=0.004, sort_every=4, ppc=(1, 1, 2))
+    ws = [dataclasses.replace(base, name=f"p{k}", nx=40 + 4 * (k % 7), nr=16 + 2 * (k % 5),
+                              w0=6.0 + 0.1 * k, seed=k) for k in range(61)]
+    steps = [12 + (k % 3) for k in range(61)]
+    mixed = [gpu_from(w, precision="fp32") for w in ws]
+    b = L.Batch(mixed, torch.cuda.Stream())
+    with pytest.raises(L.LpicError):
+        b.set_tuning(1000)                     # not a multiple of 256
+    b.set_tuning(1024)                         # several items per simulation
+    b.step([5] * len(ws))
+    b.set_tuning(8192, 5)                      # re-planned between steps, five branches
+    b.step([n - 5 for n in steps])
+    b.close()
+    for w, m, n in zip(ws, mixed, steps):
+        a = gpu_from(w, precision="fp32")
+        a.step(n)
+        assert m.counters() == a.counters()
+        assert rel_err(m.field("ex"), a.field("ex")) < 1e-5
+        assert rel_err(m.field("a"), a.field("a")) < 1e-5
 
 
 def test_served_mix_matches_alone_and_respects_budget():
