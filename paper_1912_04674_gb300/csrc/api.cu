@@ -137,7 +137,7 @@ int valid_a_count(const Phys &ph, long long c) {
 }
 
 // Host-side constants and per-row tables of one simulation.
-template <class R> Kc<R> make_consts(const Phys &ph, const R *tab_dev) {
+template <class R> Kc<R> make_consts(const Phys &ph, int nr, const R *tab_dev) {
     Kc<R> k{};
     const double dx = ph.dx, dr = ph.dr, dt = ph.dt;
     k.dt = (R)dt;
@@ -160,6 +160,7 @@ template <class R> Kc<R> make_consts(const Phys &ph, const R *tab_dev) {
     k.d_envp = 1.0 / (1.0 + dt * dt);
     k.d_envpt = dt / (1.0 + dt * dt);
     k.d_4idr = 4.0 / dr;
+    k.rmax = (R)(nr * dr);
     k.tab = tab_dev;
     return k;
 }
@@ -268,7 +269,7 @@ template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
     const Layout &L = c->L;
     S.geo = c->geo;
     S.ph = c->ph;
-    S.k = make_consts<R>(c->ph, (const R *)(c->buf + c->L.tab));
+    S.k = make_consts<R>(c->ph, c->geo.nr, (const R *)(c->buf + c->L.tab));
     S.d = c->d_desc;
     S.f.ex = (R *)(b + L.grid[0]);
     S.f.er = (R *)(b + L.grid[1]);

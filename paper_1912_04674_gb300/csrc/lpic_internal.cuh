@@ -102,6 +102,7 @@ enum RowTab : int {
 template <class R> struct Kc {
     R dt, hdt, idx, idr, dtdx, hidx, hidr, idx2, idr2, dt2, envp, envpt;
     double d_dt, d_dt2, d_idx2, d_idr2, d_hidx, d_envp, d_envpt, d_4idr;  // FP64 axis rows
+    R rmax;         // Nr dr: particles at r >= rmax leave
     const R *tab;   // NTAB x P row tables
 };
 
@@ -121,7 +122,7 @@ template <class R> struct SimDev {
 };
 
 // ---- shared device helpers -------------------------------------------------------------
-// Square roots and floors in the working precision, spelled out so that FP32 code never
+// Square roots, absolute values and floors in the working precision, spelled out so that FP32 code never
 // takes a double-precision overload.
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
@@ -129,6 +130,9 @@ template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 
 template <class R> __device__ __forceinline__ R sqrt_(R x);
 template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double sqrt_<double>(double x) { return ::sqrt(x); }
+template <class R> __device__ __forceinline__ R fabs_(R x);
+template <> __device__ __forceinline__ float fabs_<float>(float x) { return fabsf(x); }
+template <> __device__ __forceinline__ double fabs_<double>(double x) { return ::fabs(x); }
 template <class R> __device__ __forceinline__ int floor_int(R x);
 template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
 template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }

@@ -114,69 +114,58 @@ template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r,
     }
 }
 
-// FP32 deposits are summed exactly: each value is scaled by a power of two set by the largest
-// exponent among the bounds of its run (so that 32 scaled values cannot overflow 31 bits),
-// rounded to an integer, summed exactly in integers, and scaled back at the head -- one
-// rounding of 2^-24 of the run's largest bound in all.  Values q in [m*N/M, (m+1)*N/M) share
-// bound m.  Runs whose bounds are all below 2^-101 deposit nothing; a non-finite value
-// makes the run's sums NaN.
-template <int N, int M>
-__device__ __forceinline__ void run_sums_exact(const Run &r, float (&v)[N], const float (&bnd)[M]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int m = 0; m < M; m++) {
-        int e = (int)(((unsigned)__float_as_int(bnd[m]) >> 23) & 0xffu);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_down_sync(FULL, e, o);
-            if (lane + o < r.end) e = max(e, t);
-        }
-        const int emax = __shfl_sync(FULL, e, r.head);      // |v| < 2^(emax - 126)
-        const int ec = min(max(emax, 25), 254);
-        const float sc = __int_as_float((278 - ec) << 23);   // 2^(151 - emax)
-        const float isc = __int_as_float((ec - 24) << 23);   // 2^(emax - 151)
-        int qi[N / M];
-#pragma unroll
-        for (int q = 0; q < N / M; q++) qi[q] = __float2int_rn(v[m * (N / M) + q] * sc);
-        run_sums<int, N / M>(r, qi);
-#pragma unroll
-        for (int q = 0; q < N / M; q++)
-            v[m * (N / M) + q] =
-                emax < 25 ? 0.0f : (emax == 255 ? __int_as_float(0x7fffffff) : (float)qi[q] * isc);
-    }
-}
-template <int N, int M>
-__device__ __forceinline__ void run_sums_exact(const Run &r, double (&v)[N], const double (&)[M]) {
-    run_sums<double, N>(r, v);
+// q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 254), assembled from the
+// IEEE-754 fields with integer operations (the FP64 pipe is slow on this part): the leading
+// one of |q| is moved to bit 52 and the exponent added on top of it.
+__device__ __forceinline__ double scaled_int_to_double(int q, int e) {
+    const unsigned long long sgn = q < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned a = q < 0 ? 0u - (unsigned)q : (unsigned)q;
+    const int lz = __clz(a);                                          // leading one at bit 31 - lz
+    const unsigned long long m = (unsigned long long)a << (lz + 21);   // leading one at bit 52
+    const unsigned long long ex = (unsigned long long)(1023 + (31 - lz) + (e - 151) - 1) << 52;
+    return __longlong_as_double((long long)((ex + m) | sgn));
 }
 
-// The run's four deposits (sums at the head) go to addr[q] scaled by fac[q].  In FP32 a run of
-// four or more lanes spreads them over its first four lanes (one conversion and one atomic
-// each); shorter runs, and FP64, issue them from the head.
-__device__ __forceinline__ void run_atomics(const Run &r, unsigned key, const float (&v)[4],
-                                            double *const (&addr)[4], const float (&fac)[4]) {
-    const int lane = threadIdx.x & 31, rank = lane - r.head;
-    float s[4];
+// Deposit of each run's four values (row factors already applied; the lanes of a run share
+// the key, hence the addresses) to addr[q] in FP64.
+// FP32: summed exactly.  Value q belongs to group m = q*M/4 with bound bnd[m] >= |value|; every
+// value of group m in the warp is scaled by 2^(151 - e_m), e_m the largest exponent field among
+// the warp's group-m bounds (so that 32 scaled values cannot overflow 31 bits), rounded to an
+// integer (one rounding of at most 2^-25 of the warp's largest bound), and the run's integers
+// are summed exactly; the head lane turns each sum into FP64 exactly and adds it.  A
+// non-finite value in the warp makes its group's deposits NaN.
+template <int M>
+__device__ __forceinline__ void run_deposit(const Run &r, unsigned key, const float (&v)[4], const float (&bnd)[M],
+                                            double *const (&addr)[4]) {
+    int qi[4], ec[M];
+    bool bad[M];
 #pragma unroll
-    for (int q = 0; q < 4; q++) s[q] = __shfl_sync(FULL, v[q], r.head);
-    if (key == kNoKey) return;
-    if (r.end - r.head >= 4) {
-        if (rank < 4) {
-            const float val = rank == 0 ? s[0] * fac[0] : rank == 1 ? s[1] * fac[1]
-                            : rank == 2 ? s[2] * fac[2] : s[3] * fac[3];
-            double *const a = rank == 0 ? addr[0] : rank == 1 ? addr[1] : rank == 2 ? addr[2] : addr[3];
-            atom_add(a, val);
-        }
-    } else if (rank == 0) {
+    for (int m = 0; m < M; m++) {
+        const unsigned e = ((unsigned)__float_as_uint(bnd[m]) >> 23) & 0xffu;
+        const int emax = (int)__reduce_max_sync(FULL, e);
+        bad[m] = emax == 255;
+        ec[m] = min(max(emax, 25), 254);
+        const float sc = __uint_as_float((unsigned)(278 - ec[m]) << 23);   // 2^(151 - ec)
 #pragma unroll
-        for (int q = 0; q < 4; q++) atom_add(addr[q], s[q] * fac[q]);
+        for (int q = m * 4 / M; q < (m + 1) * 4 / M; q++) qi[q] = bad[m] ? 0 : __float2int_rn(v[q] * sc);
     }
-}
-__device__ __forceinline__ void run_atomics(const Run &r, unsigned key, const double (&v)[4],
-                                            double *const (&addr)[4], const double (&fac)[4]) {
+    run_sums<int, 4>(r, qi);
     if (key == kNoKey || (int)(threadIdx.x & 31) != r.head) return;
 #pragma unroll
-    for (int q = 0; q < 4; q++) atom_add(addr[q], v[q] * fac[q]);
+    for (int q = 0; q < 4; q++) {
+        const int m = q * M / 4;
+        if (bad[m]) atomicAdd(addr[q], __longlong_as_double(0x7ff8000000000000ll));
+        else if (qi[q] != 0) atomicAdd(addr[q], scaled_int_to_double(qi[q], ec[m]));
+    }
+}
+template <int M>
+__device__ __forceinline__ void run_deposit(const Run &r, unsigned key, const double (&v)[4], const double (&)[M],
+                                            double *const (&addr)[4]) {
+    double s[4] = {v[0], v[1], v[2], v[3]};
+    run_sums<double, 4>(r, s);
+    if (key == kNoKey || (int)(threadIdx.x & 31) != r.head) return;
+#pragma unroll
+    for (int q = 0; q < 4; q++) atom_add(addr[q], s[q]);
 }
 
 // Particle registers of one slot.
@@ -262,11 +251,12 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
         const R sz = pz + hdt * (q * Ez - Gz * i2g0);
         const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
 
-        // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1); the 1/V factor
-        // is applied per row after the run sum
+        // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1), 1/V per row
+        const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
         const R base_w = alive ? w * rgt : (R)0;
-        R v[4] = {base_w * w00, base_w * w10, base_w * w01, base_w * w11};
-        const R bnd[1] = {base_w};
+        const R c0 = base_w * i0, c1 = base_w * i1;
+        const R v[4] = {c0 * w00, c0 * w10, c1 * w01, c1 * w11};
+        const R bnd[1] = {c0 > c1 ? c0 : c1};
         const unsigned key = alive ? (unsigned)b : kNoKey;
 
         const R i2gt = (R)0.5 * rgt;
@@ -286,12 +276,9 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
             P.pz[k] = mz + (ppx * vy) + hdt * Fz;
         }
         const Run run = run_of(key);
-        run_sums_exact<4, 1>(run, v, bnd);
-        const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
         double *const addr[4] = {S.f.chi + b, S.f.chi + b + geo.P, S.f.chi + b + 1,
                                  S.f.chi + b + geo.P + 1};
-        const R fac[4] = {i0, i0, i1, i1};
-        run_atomics(run, key, v, addr, fac);
+        run_deposit<1>(run, key, v, bnd, addr);
         cur = nxt;
     }
 }
@@ -384,7 +371,7 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
     const long long shift = S.d->shift, step = S.d->step;
     const int snext = window_shifts(S.ph, step, shift) ? 1 : 0;
     const R dt = S.k.dt, idr = S.k.idr, dtdx = S.k.dtdx;
-    const R rmax = (R)(geo.nr * S.ph.dr);
+    const R rmax = S.k.rmax;
     const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
     const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -431,8 +418,11 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
         const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
         const bool fast = alive && stays;
         const R bx = fast ? w * ddx : (R)0, br = fast ? w * ddr : (R)0;
-        R v[4] = {-bx * ((R)1 - rbar), -bx * rbar, -br * ((R)1 - xbar), -br * xbar};
-        const R bnd[2] = {bx, br};
+        // row factors 1/(dt A_j) of the two x faces and 1/(dt 2 pi r_{j+1/2} dx) of the r face
+        const R fx0 = tjx[ja], fx1 = tjx[ja + 1], fr = tjr[ja];
+        const R cx = -bx, cr = -br * fr;
+        const R v[4] = {cx * ((R)1 - rbar) * fx0, cx * rbar * fx1, cr * ((R)1 - xbar), cr * xbar};
+        const R bnd[2] = {fabs_<R>(bx) * (fx0 > fx1 ? fx0 : fx1), fabs_<R>(cr)};
         const int b = geo.at(off, ia, ja);
         const unsigned key = fast ? (unsigned)b : kNoKey;
 
@@ -471,11 +461,8 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
             P.z[k] = z1;
         }
         const Run run = run_of(key);
-        run_sums_exact<4, 2>(run, v, bnd);
-        const R tr = tjr[ja];
         double *const addr[4] = {S.f.jx + b, S.f.jx + b + 1, S.f.jr + b, S.f.jr + b + geo.P};
-        const R fac[4] = {tjx[ja], tjx[ja + 1], tr, tr};
-        run_atomics(run, key, v, addr, fac);
+        run_deposit<2>(run, key, v, bnd, addr);
         // at most 32 join per iteration, so draining at 32 keeps the queue within QW
         if (queued >= 32) {
             drain_queue<R>(S, off, Q, wq, queued);
