@@ -94,29 +94,38 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
-        self.gpu, self.rows, self.stop_ev = gpu, [], threading.Event()
+    def __init__(self, gpu: int, period_ms: int = 50):
+        self.gpu, self.period, self.rows, self.proc = gpu, period_ms, [], None
         self.t = threading.Thread(target=self._run, daemon=True)
 
     def _run(self):
-        while not self.stop_ev.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([v.strip() for v in out.split(",")])
-            except Exception:
-                return
-            self.stop_ev.wait(0.2)
+        try:
+            for line in self.proc.stdout:
+                line = line.strip()
+                if line:
+                    self.rows.append([v.strip() for v in line.split(",")])
+        except Exception:
+            return
 
     def __enter__(self):
-        self.t.start()
+        # one nvidia-smi process streaming a sample every period_ms (our own child, ended below)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", f"--loop-ms={self.period}"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.stop_ev.set()
-        self.t.join(timeout=10)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=5)
 
     def summary(self):
         if not self.rows:
@@ -131,9 +140,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- our arm
-def make_sim(prec: str, w=WORKLOAD, sort_every=None):
+def make_sim(prec: str, w=WORKLOAD, sort_every=None, track=False):
     from paper_1912_04674_gb300 import lpic as L
-    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, sort_every or w.sort_every)
+    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, sort_every or w.sort_every, track_continuity=track)
     return L.Simulation(g, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
                         L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), precision=prec)
 
@@ -261,16 +270,30 @@ def accuracy(k_total: int, horizon: int = 300):
     inside the predictability horizon, and the settled-state errors are reported beside the
     FP64 spread."""
     import numpy as np
-    s64, s64b, s32 = make_sim("fp64"), make_sim("fp64", sort_every=19), make_sim("fp32")
+    s64 = make_sim("fp64", track=True)
+    s64b = make_sim("fp64", sort_every=19, track=True)
+    s32 = make_sim("fp32", track=True)
+
+    def accel(s):
+        n, wsum, mean, rms = (float(v) for v in s.accel_energy())
+        return {"count": int(n), "mean_gamma_minus_1": mean, "rms_gamma_minus_1": rms}
+
+    def rel(a, b):
+        return float(abs(a / b - 1)) if b else (0.0 if a == b else None)
 
     def errs():
         e64 = s64.ex_axis()
         n = max(np.linalg.norm(e64), 1e-300)
         a64 = s64.a_abs_max()
+        acc64, acc32, acc64b = accel(s64), accel(s32), accel(s64b)
         return {"fp32_wake_ex_rel_l2": float(np.linalg.norm(s32.ex_axis() - e64) / n),
                 "fp32_a_max_rel": float(abs(s32.a_abs_max() / a64 - 1)),
                 "fp64_reordered_wake_ex_rel_l2": float(np.linalg.norm(s64b.ex_axis() - e64) / n),
-                "fp64_reordered_a_max_rel": float(abs(s64b.a_abs_max() / a64 - 1))}
+                "fp64_reordered_a_max_rel": float(abs(s64b.a_abs_max() / a64 - 1)),
+                "continuity_residual": {"fp64": s64.cont_residual(), "fp32": s32.cont_residual()},
+                "accelerated_electrons": {"fp64": acc64, "fp32": acc32, "fp64_reordered": acc64b,
+                                          "fp32_mean_rel": rel(acc32["mean_gamma_minus_1"], acc64["mean_gamma_minus_1"]),
+                                          "fp32_rms_rel": rel(acc32["rms_gamma_minus_1"], acc64["rms_gamma_minus_1"])}}
 
     for s in (s64, s64b, s32):
         s.step(horizon)
@@ -346,6 +369,26 @@ def batched_scan(n_sims: int, steps: int, warmup: int = 5):
             "per_sim_streams_ms_per_step": ms_streams,
             "workload": "64 scan sims: Nx~U{256..2048}, Nr~U{64..256}, a0~U[0.5,3], "
                         "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc, FP32_MIXED, early steps"}
+
+
+def large_run(steps: int = 30, warmup: int = 20):
+    """The large single run (8192 x 512 cells, 67,108,864 electrons) in both precisions:
+    early steps (the pulse already sits in the plasma that fills the initial window)."""
+    import torch
+
+    import workloads
+    out = {"workload": workloads.C3.name, "particles": workloads.C3.particles, "steps": steps}
+    for prec in ("fp32", "fp64"):
+        sim = make_sim(prec, w=workloads.C3)
+        sim.step(warmup)
+        ms, alive = timed_steps(sim, steps)
+        out[prec] = {"ms_per_step": ms / steps, "value": alive * steps / (ms * 1e-3),
+                     "unit": "particle-steps/s"}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def cpu_baseline(max_seconds=20.0):
@@ -436,6 +479,7 @@ def run_ours(args):
     e2e = e2e_run("fp32", args.steps, args.settle) if extras else None
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
     batch = batched_scan(args.batch_sims, args.batch_steps) if (extras and args.batch_sims > 0) else None
+    large = large_run() if (extras and not args.no_large) else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
@@ -460,7 +504,7 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "scan": scan, "gpu_launches": r32["gpu_launches"],
+            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "batch": batch, "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -507,7 +551,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -517,6 +561,7 @@ def main():
                     help="untimed steps before the timed region (developed wake)")
     ap.add_argument("--save-state", default=None, help="save the settled state (npz)")
     ap.add_argument("--load-state", default=None, help="start from a saved state instead of settling")
+    ap.add_argument("--no-large", action="store_true", help="skip the 67M-electron run")
     ap.add_argument("--batch-sims", type=int, default=64,
                     help="simulations in the batched-scan measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=60)

@@ -73,7 +73,7 @@ template <class R> __global__ void k_prepass(SimDev<R> S) { prepass_tile<R>(S, b
 // inv2rj = 1/(2 dr r_j) (unused on the axis row, whose radial part is 4 (A_1 - A_0)/dr^2).
 template <class C, class V>
 __device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V rmin, V amin,
-                                              double chi_d, bool axis, C idx2, C idr2, C inv2rj,
+                                              C chi, bool axis, C idx2, C idr2, C inv2rj,
                                               C hidx, C t, C t2, C p, C pt, C &ore, C &oim) {
     const C cx = (C)cin.x, cy = (C)cin.y;
     const C xpx = (C)xpin.x, xpy = (C)xpin.y, xmx = (C)xmin.x, xmy = (C)xmin.y;
@@ -88,7 +88,6 @@ __device__ __forceinline__ void envelope_node(V cin, V xpin, V xmin, V rpin, V r
         ly += (rpy - (C)2 * cy + rmy) * idr2 + (rpy - rmy) * inv2rj;
     }
     const C dxr = (xpx - xmx) * hidx, dxi = (xpy - xmy) * hidx;
-    const C chi = (C)chi_d;
     const C amx = (C)amin.x, amy = (C)amin.y;
     // bracket: lap - chi A + 2i dA/dx
     const C bx = lx - chi * cx - (C)2 * dxi;
@@ -113,16 +112,16 @@ template <class R> __device__ __forceinline__ void envelope_store(const SimDev<R
 
 template <class R> __device__ __forceinline__ void envelope_axis_node(const SimDev<R> &S, int i);
 
-// Tile (bx, by): off-axis nodes j = 1 + bx*BX + tx, i = by*BY + ty; an axis tile takes the
-// axis row of columns by*BY + ty (one node per warp row, FP64), so that its long FP64 chains
-// run spread over the SMs beside the FP32 tiles.
+// Tile (bx, by): off-axis nodes j = 1 + bx*BX + tx, i = by*BY + ty; axis tile by takes the
+// axis nodes i = by*BX*BY + (ty*BX + tx), one per thread (FP64), so that every lane of its
+// warps does FP64 work (only the first ceil((Nx+1)/(BX*BY)) axis tiles have nodes).
 template <class R>
 __device__ __forceinline__ void envelope_tile(const SimDev<R> &S, int bx, int by, bool axis) {
     const Geo g = S.geo;
     const int off = S.d->off;
     if (axis) {
-        const int i = by * BY + threadIdx.y;
-        if (threadIdx.x == 0 && i <= g.nx) envelope_axis_node<R>(S, i);
+        const int i = by * BX * BY + threadIdx.y * BX + threadIdx.x;
+        if (i <= g.nx) envelope_axis_node<R>(S, i);
         return;
     }
     const int j = 1 + bx * BX + threadIdx.x;
@@ -135,7 +134,7 @@ __device__ __forceinline__ void envelope_tile(const SimDev<R> &S, int bx, int by
     const Kc<R> &K = S.k;
     R nre, nim;
     envelope_node<R>(c, A[g.at(off, i + 1, j)], A[g.at(off, i - 1, j)], A[id + 1], A[id - 1],
-                     S.f.a[ab ^ 1][id], S.f.chi[id], false, K.idx2, K.idr2,
+                     S.f.a[ab ^ 1][id], from_acc<R>(S.f.chi[id]), false, K.idx2, K.idr2,
                      K.tab[T_ENV1R * g.P + j], K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
     envelope_store<R>(S, id, ab, c, nre, nim);
 }
@@ -175,7 +174,7 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.er[id] = (R)0;
         } else {
             R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * S.k.idx;
-            S.f.er[id] += dt * (-dbdx - (R)S.f.jr[id]);
+            S.f.er[id] += dt * (-dbdx - from_acc<R>(S.f.jr[id]));
         }
     }
     if (i < g.nx) {
@@ -186,7 +185,7 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jx[id]));
         } else {
             R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
-            S.f.ex[id] += dt * (curl - (R)S.f.jx[id]);
+            S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jx[id]));
         }
     }
 }

@@ -133,6 +133,28 @@ template <> __device__ __forceinline__ double sqrt_<double>(double x) { return :
 template <class R> __device__ __forceinline__ R fabs_(R x);
 template <> __device__ __forceinline__ float fabs_<float>(float x) { return fabsf(x); }
 template <> __device__ __forceinline__ double fabs_<double>(double x) { return ::fabs(x); }
+// FP64 accumulator -> working precision.  For FP32, round to nearest even from the IEEE-754
+// fields with integer operations (the FP64 pipe, which the hardware conversion would use, is
+// slow on this part); magnitudes below the FP32 normal range flush to a signed zero, like the
+// FP32 kernels' arithmetic; overflow gives infinity and NaN stays NaN.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const unsigned sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;        // FP32 exponent field
+    const unsigned mf = ((hi & 0xfffffu) << 3) | (lo >> 29);      // top 23 of 52 mantissa bits
+    const unsigned rest = lo & 0x1fffffffu, half = 0x10000000u;   // the 29 dropped bits
+    const unsigned up = (rest > half || (rest == half && (mf & 1u))) ? 1u : 0u;
+    const unsigned fin = ((unsigned)e << 23) + mf + up;           // a carry rounds into the exponent
+    const bool special = ((hi >> 20) & 0x7ffu) == 0x7ffu;
+    const unsigned nan_or_inf = 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+    const unsigned bits = special ? nan_or_inf : (e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : fin));
+    return __uint_as_float(sgn | bits);
+}
+template <class R> __device__ __forceinline__ R from_acc(double x);
+template <> __device__ __forceinline__ float from_acc<float>(double x) { return d2f_bits(x); }
+template <> __device__ __forceinline__ double from_acc<double>(double x) { return x; }
+
 template <class R> __device__ __forceinline__ int floor_int(R x);
 template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
 template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
