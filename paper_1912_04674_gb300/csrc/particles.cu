@@ -115,15 +115,18 @@ template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r,
 }
 
 // q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 254), assembled from the
-// IEEE-754 fields with integer operations (the FP64 pipe is slow on this part): the leading
-// one of |q| is moved to bit 52 and the exponent added on top of it.
+// IEEE-754 fields with 32-bit integer operations (the FP64 pipe is slow on this part): |q| is
+// normalised so that its leading one sits at bit 31, the 31 bits below it become the top of
+// the 52-bit fraction, and the exponent is the position of that one plus e - 151.
 __device__ __forceinline__ double scaled_int_to_double(int q, int e) {
-    const unsigned long long sgn = q < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned sgn = (unsigned)q & 0x80000000u;
     const unsigned a = q < 0 ? 0u - (unsigned)q : (unsigned)q;
-    const int lz = __clz(a);                                          // leading one at bit 31 - lz
-    const unsigned long long m = (unsigned long long)a << (lz + 21);   // leading one at bit 52
-    const unsigned long long ex = (unsigned long long)(1023 + (31 - lz) + (e - 151) - 1) << 52;
-    return __longlong_as_double((long long)((ex + m) | sgn));
+    const int lz = __clz(a);
+    const unsigned n = a << lz;                                        // leading one at bit 31
+    const unsigned ex = (unsigned)(1023 + (31 - lz) + (e - 151));
+    const unsigned hi = sgn | (ex << 20) | ((n >> 11) & 0xfffffu);
+    const unsigned lo = n << 21;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // Deposit of each run's four values (row factors already applied; the lanes of a run share
