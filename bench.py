@@ -569,6 +569,8 @@ def main():
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
+    ap.add_argument("--only", choices=("batch", "large"), default=None,
+                    help="run one leg alone and print its object (a profiling run, not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -577,6 +579,12 @@ def main():
         return
     from paper_1912_04674_gb300 import build
     build.build()
+    if args.only == "batch":
+        print(json.dumps({"profile_run": True, "batch": batched_scan(args.batch_sims, args.batch_steps)}))
+        return
+    if args.only == "large":
+        print(json.dumps({"profile_run": True, "large_run": large_run()}))
+        return
     run_ours(args)
 
 

@@ -233,7 +233,7 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
  *   multiple of 256 in [1024, 1048576]; default 4096).  Smaller items balance the blocks
  *   better, larger ones cost less per item.
  * packs: split the simulations into this many packs (0: as few as the parameter space
- *   allows, one per 56 simulations), each with its own launch sequence as a parallel branch
+ *   allows, one per 48 simulations), each with its own launch sequence as a parallel branch
  *   of the graph, so that phases of different packs overlap on the device.
  * The binding's autotuner picks both by timing real steps.  Errors: LPIC_EINVAL. */
 lpic_status lpic_batch_set_tuning(lpic_batch *b, int32_t particles_per_item, int32_t packs);

@@ -161,6 +161,11 @@ template <class R> Kc<R> make_consts(const Phys &ph, int nr, const R *tab_dev) {
     k.d_envpt = dt / (1.0 + dt * dt);
     k.d_4idr = 4.0 / dr;
     k.rmax = (R)(nr * dr);
+    k.lat_ippcx = (R)ph.inv_ppcx;
+    k.lat_ippcr = (R)ph.inv_ppcr;
+    k.lat_ippct = (R)ph.inv_ppct;
+    k.lat_dr = (R)dr;
+    k.lat_wfac = (R)ph.wfac;
     k.tab = tab_dev;
     return k;
 }
@@ -225,9 +230,11 @@ struct lpic_ctx {
         err = std::string(where) + ": " + cudaGetErrorString(e);
         return LPIC_ECUDA;
     }
-    void sync_views() {
+    void sync_views() {   // after a change of the physics parameters (plasma loading)
         sd.ph = ph;
         sf.ph = ph;
+        sd.k = make_consts<double>(ph, geo.nr, sd.k.tab);
+        sf.k = make_consts<float>(ph, geo.nr, sf.k.tab);
     }
     template <class F> void dispatch(F &&f) {
         if (prec == LPIC_FP64) f(sd); else f(sf);

@@ -103,6 +103,7 @@ template <class R> struct Kc {
     R dt, hdt, idx, idr, dtdx, hidx, hidr, idx2, idr2, dt2, envp, envpt;
     double d_dt, d_dt2, d_idx2, d_idr2, d_hidx, d_envp, d_envpt, d_4idr;  // FP64 axis rows
     R rmax;         // Nr dr: particles at r >= rmax leave
+    R lat_ippcx, lat_ippcr, lat_ippct, lat_dr, lat_wfac;   // plasma lattice (1/ppc, dr, 2 pi dr dx / ppc)
     const R *tab;   // NTAB x P row tables
 };
 
@@ -186,51 +187,71 @@ __host__ __device__ __forceinline__ bool window_shifts(const Phys &ph, long long
     return ph.moving_window && (double)(n + 1) * ph.dt >= (double)(s + 1) * ph.dx;
 }
 
-// Lattice particle of lab column c (paper Sec. 4 plasma sampling; regular ppc lattice):
-// local index enumerates (j, a valid, b, k); returns false if beyond the column's count.
+// Plasma lattice of lab column c (regular ppc_x x ppc_r x ppc_theta per cell, weight
+// n(x) 2 pi r dr dx / ppc; the densities of the Sec. 4 runs): the x slices a that carry
+// plasma and their densities, computed once per column.
+template <class R> struct ColumnPlan {
+    int nv;
+    int valid[16];
+    R dens[16];
+};
 template <class R>
-__device__ __forceinline__ bool lattice_particle(const SimDev<R> &S, long long c, int local,
-                                                 int slot) {
+__device__ __forceinline__ void column_plan(const Phys &ph, long long c, ColumnPlan<R> &cp) {
+    cp.nv = 0;
+    for (int a = 0; a < ph.ppcx && a < 16; a++) {
+        const double n = plasma_density(ph, lattice_x(ph, c, a));
+        if (n > 0.0) {
+            cp.valid[cp.nv] = a;
+            cp.dens[cp.nv] = (R)n;
+            cp.nv++;
+        }
+    }
+}
+template <class R> __device__ __forceinline__ int column_particles(const Phys &ph, const ColumnPlan<R> &cp, int nr) {
+    return cp.nv * ph.ppcr * ph.ppct * nr;
+}
+
+// Particle `local` of column c (enumerating (j, valid slice, b, k)) into `slot`; local must be
+// below column_particles.  FP64 evaluates the lattice in FP64; FP32 in FP32 (its positions are
+// FP32 anyway), with the azimuthal offset u from the top 24 bits of the SplitMix64 output.
+template <class R>
+__device__ __forceinline__ void lattice_emit(const SimDev<R> &S, const ColumnPlan<R> &cp, long long c, int local,
+                                             int slot) {
     const Phys &ph = S.ph;
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
-    int valid[16];
-    int nv = 0;
-    for (int a = 0; a < ph.ppcx && a < 16; a++)
-        if (plasma_density(ph, lattice_x(ph, c, a)) > 0.0) valid[nv++] = a;
-    const int perj = nv * ph.ppcr * ph.ppct;
-    if (perj == 0 || local >= perj * S.geo.nr) return false;
+    const int perj = cp.nv * ph.ppcr * ph.ppct;
     const int j = local / perj;
     int rem = local - j * perj;
     const int av = rem / (ph.ppcr * ph.ppct);
     rem -= av * ph.ppcr * ph.ppct;
     const int b = rem / ph.ppct, kk = rem - b * ph.ppct;
-    const int a = valid[av];
-    const double n = plasma_density(ph, lattice_x(ph, c, a));
-    const double r = (j + (b + 0.5) * ph.inv_ppcr) * ph.dr;
+    const int a = cp.valid[av];
     const unsigned long long cell = (unsigned long long)c * S.geo.nr + (unsigned long long)j;
-    const double u = (double)(splitmix64(ph.seed, cell + 1) >> 11) * (1.0 / 9007199254740992.0);
-    R sn, cs;
-    if (sizeof(R) == 4) {   // FP32 positions: the angle in FP32 is as exact as they are
-        float sf, cf;
-        sincosf((float)(2.0 * kPi * ((kk + u) * ph.inv_ppct)), &sf, &cf);
-        sn = (R)sf;
-        cs = (R)cf;
+    const unsigned long long h = splitmix64(ph.seed, cell + 1);
+    if (sizeof(R) == 4) {
+        const float r = ((float)j + ((float)b + 0.5f) * (float)S.k.lat_ippcr) * (float)S.k.lat_dr;
+        const float u = (float)(unsigned)(h >> 40) * 5.9604644775390625e-08f;   // 2^-24
+        float sn, cs;
+        sincospif(2.0f * ((float)kk + u) * (float)S.k.lat_ippct, &sn, &cs);
+        P.ox[slot] = (R)(((float)a + 0.5f) * (float)S.k.lat_ippcx);
+        P.y[slot] = (R)(r * cs);
+        P.z[slot] = (R)(r * sn);
+        P.w[slot] = (R)((float)cp.dens[av] * r * (float)S.k.lat_wfac);
     } else {
+        const double r = (j + (b + 0.5) * ph.inv_ppcr) * ph.dr;
+        const double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
         double sd, cd;
         sincos(2.0 * kPi * ((kk + u) * ph.inv_ppct), &sd, &cd);
-        sn = (R)sd;
-        cs = (R)cd;
+        P.ox[slot] = (R)((a + 0.5) * ph.inv_ppcx);
+        P.y[slot] = (R)(r * cd);
+        P.z[slot] = (R)(r * sd);
+        P.w[slot] = (R)((double)cp.dens[av] * r * ph.wfac);
     }
     P.ix[slot] = (int)c;
-    P.ox[slot] = (R)((a + 0.5) * ph.inv_ppcx);
-    P.y[slot] = (R)r * cs;
-    P.z[slot] = (R)r * sn;
     P.px[slot] = (R)0;
     P.py[slot] = (R)0;
     P.pz[slot] = (R)0;
-    P.w[slot] = (R)(n * r * ph.wfac);
     P.id[slot] = ((cell * ph.ppcx + a) * ph.ppcr + b) * ph.ppct + kk;
-    return true;
 }
 
 // ---- launchers (defined in the kernel translation units) --------------------------------
@@ -251,8 +272,8 @@ template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStr
 // The views of the simulations of one fused launch travel by value in the kernel's
 // parameter space (a __grid_constant__ pack, read through the constant cache like a single
 // simulation's view, so the bodies keep the register budget of the single kernels).
-// 52 views of at most 592 bytes plus the other arguments fit the 32,764-byte limit.
-constexpr int kPackMax = 52;
+// 48 views of at most 640 bytes plus the other arguments fit the 32,764-byte limit.
+constexpr int kPackMax = 48;
 template <class R> struct SimPack { SimDev<R> v[kPackMax]; };
 static_assert(sizeof(SimPack<double>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764 &&
                   sizeof(SimPack<float>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764,

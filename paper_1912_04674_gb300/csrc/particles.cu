@@ -507,7 +507,9 @@ __global__ void k_load_columns(SimDev<R> S, const int *__restrict__ colbase, int
             int mid = (lo + hi) >> 1;
             if (colbase[mid] <= t) lo = mid; else hi = mid;
         }
-        lattice_particle<R>(S, s + lo, t - colbase[lo], t);
+        ColumnPlan<R> cp;
+        column_plan<R>(S.ph, s + lo, cp);
+        if (t - colbase[lo] < column_particles<R>(S.ph, cp, S.geo.nr)) lattice_emit<R>(S, cp, s + lo, t - colbase[lo], t);
     }
 }
 

@@ -8,14 +8,6 @@ namespace {
 
 constexpr int TPB = 256;
 
-// Injected particles in the new last cell column of lab column c.
-__device__ __forceinline__ int column_count(const Phys &ph, long long c, int nr) {
-    int nv = 0;
-    for (int a = 0; a < ph.ppcx; a++)
-        if (plasma_density(ph, lattice_x(ph, c, a)) > 0.0) nv++;
-    return nv * ph.ppcr * ph.ppct * nr;
-}
-
 // End of step n.  If the window shifts (paper Sec. 4 runs use a window moving at c), the live
 // window slides one physical column, the guard columns of the persistent arrays on both
 // sides of the new window are zeroed (the new front column of A and Er is among them), and
@@ -48,10 +40,14 @@ template <class R> __device__ __forceinline__ void window_body(const SimDev<R> &
             S.f.a[1][id] = zc;
         }
         if (S.ph.have_plasma) {
-            count = column_count(S.ph, c, g.nr);
+            // the column's lattice slices and densities, once per block
+            __shared__ ColumnPlan<R> cp;
+            if (threadIdx.x == 0) column_plan<R>(S.ph, c, cp);
+            __syncthreads();
+            count = column_particles<R>(S.ph, cp, g.nr);
             inject = np + count <= S.ph.cap;
             if (inject)
-                for (int t = tid; t < count; t += nth) lattice_particle<R>(S, c, t, np + t);
+                for (int t = tid; t < count; t += nth) lattice_emit<R>(S, cp, c, t, np + t);
         }
     }
     // last block: advance the counters once every block is done with them
