@@ -45,7 +45,18 @@ KEYS = [
     ("smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "stall long scoreboard"),
     ("smsp__average_warps_issue_stalled_branch_resolving_per_issue_active.ratio", "stall branch resolving"),
     ("smsp__average_warps_issue_stalled_wait_per_issue_active.ratio", "stall wait"),
+    ("smsp__average_warps_issue_stalled_short_scoreboard_per_issue_active.ratio", "stall short scoreboard"),
+    ("smsp__average_warps_issue_stalled_not_selected_per_issue_active.ratio", "stall not selected"),
+    ("sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active", "XU pipe %"),
+    ("smsp__sass_thread_inst_executed_op_dfma_pred_on.sum", "FP64 FMA (thread inst)"),
+    ("smsp__sass_thread_inst_executed_op_dmul_pred_on.sum", "FP64 MUL (thread inst)"),
+    ("smsp__sass_thread_inst_executed_op_dadd_pred_on.sum", "FP64 ADD (thread inst)"),
+    ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active", "FP64 pipe cycles %"),
 ]
+
+# kernels of the time step (the rest of a launch list is set-up and diagnostics)
+STEP = ("k_prepass", "k_pass_a", "k_envelope", "k_pass_b", "k_ampere", "k_window", "k_sort_",
+        "k_scan_", "k_relocate")
 
 
 def short(name: str) -> str:
@@ -68,12 +79,15 @@ def launches(path, title, command):
         tot[k] += v * scale
         cnt[k] += 1
     allt = sum(tot.values())
+    stept = sum(t for k, t in tot.items() if k.startswith(STEP)) or 1.0
     out = [f"# {title}", "", f"Command: `{command}`", "",
            "ncu `--metrics gpu__time_duration.sum --clock-control none` launch list (every launch of",
-           "the run; cold-cache and serialised, so shares, not absolute times, carry over).", "",
-           "| kernel | launches | total us | share |", "|---|---|---|---|"]
+           "the run; cold-cache and serialised, so shares, not absolute times, carry over).",
+           "`step share`: share among the time-step kernels only (set-up and diagnostics excluded).", "",
+           "| kernel | launches | total us | share | step share |", "|---|---|---|---|---|"]
     for k, t in sorted(tot.items(), key=lambda kv: -kv[1]):
-        out.append(f"| {k} | {cnt[k]} | {t:.1f} | {t / allt:.3f} |")
+        ss = f"{t / stept:.3f}" if k.startswith(STEP) else "-"
+        out.append(f"| {k} | {cnt[k]} | {t:.1f} | {t / allt:.3f} | {ss} |")
     return "\n".join(out) + "\n"
 
 
@@ -83,9 +97,9 @@ def raw(rep):
     return rows[0], rows[1], rows[2:]
 
 
-def capture(rep, title, command):
+def capture(rep, title, command, how="--set full"):
     hdr, units, rows = raw(rep)
-    out = [f"# {title}", "", f"Command: `{command}`", "", "ncu `--set full --clock-control none` capture.", ""]
+    out = [f"# {title}", "", f"Command: `{command}`", "", f"ncu `{how} --clock-control none` capture.", ""]
     names = [short(r[hdr.index("Kernel Name")]) for r in rows]
     out.append("| counter | " + " | ".join(names) + " |")
     out.append("|---|" + "---|" * len(names))
@@ -119,6 +133,6 @@ if __name__ == "__main__":
     if mode == "launches":
         print(launches(*sys.argv[2:5]))
     elif mode == "capture":
-        print(capture(*sys.argv[2:5]))
+        print(capture(*sys.argv[2:6]))
     else:
         print(traffic(*sys.argv[2:4]))
