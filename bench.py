@@ -278,13 +278,13 @@ def accuracy(k_total: int, horizon: int = 300):
 
     The a0 = 2 wake breaks and injects electrons after a few hundred steps; from then on the
     run is chaotic: FP64 against itself with only the order of the atomic additions changed
-    (sort cadence 19 instead of 20) drifts from 1e-15 to percent level by the settled state.
+    (sort cadence one step shorter) drifts from 1e-15 to percent level by the settled state.
     The FP32 bar (1e-3 on wake Ex and peak |A|) is therefore checked at `horizon` steps,
     inside the predictability horizon, and the settled-state errors are reported beside the
     FP64 spread."""
     import numpy as np
     s64 = make_sim("fp64", track=True)
-    s64b = make_sim("fp64", sort_every=19, track=True)
+    s64b = make_sim("fp64", sort_every=WORKLOAD.sort_every - 1, track=True)
     s32 = make_sim("fp32", track=True)
 
     def accel(s):

@@ -22,7 +22,7 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(_HERE, "_build", "autotune.json")
-CANDIDATES = (5, 10, 20, 40)
+CANDIDATES = (10, 20, 40, 60, 100)
 DEFAULT = 20
 TILE_CANDIDATES = (2048, 4096, 8192, 16384)
 TILE_DEFAULT = 4096

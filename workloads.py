@@ -48,11 +48,14 @@ C1 = Workload("c1_fp64_256x64", nx=256, nr=64, dx=0.69, dr=1.5, dt=0.8 * 0.69, s
               a0=0.1, w0=30.0, L=20.0, n0=0.0017)
 # Single run FP32 vs FP64: 2048 x 256 cells, 8,388,608 electrons, 200-cell up-ramp at the
 # back of the initial window, nonlinear driver.
+# Sort cadence 60: measured at the developed wake (step 2600), the step time falls from
+# 0.377 ms at k = 5 to 0.333 at k = 20 and 0.320 at k = 60 (0.319 at k = 100): background
+# electrons keep their lab cells, so runs of equal cells survive many steps between sorts.
 C2 = Workload("c2_2048x256_8.4M", nx=2048, nr=256, dx=0.69, dr=1.5, dt=0.8 * 0.69, steps=5000,
-              a0=2.0, w0=60.0, L=25.0, n0=0.0017, ramp_cells=200)
+              a0=2.0, w0=60.0, L=25.0, n0=0.0017, ramp_cells=200, sort_every=60)
 # Large single run: 8192 x 512 cells, 67,108,864 electrons.
 C3 = Workload("c3_8192x512_67M", nx=8192, nr=512, dx=0.69, dr=1.5, dt=0.8 * 0.69, steps=10000,
-              a0=3.0, w0=80.0, L=30.0, n0=0.001)
+              a0=3.0, w0=80.0, L=30.0, n0=0.001, sort_every=60)
 
 ALL = {w.name: w for w in (C1, C2, C3)}
 
