@@ -58,6 +58,8 @@ typedef struct osim {
     double n0, x_start, ramp_len;
     int ppcx, ppcr, ppct;
     uint64_t seed;
+    /* current filter: passes of the binomial filter after the deposit (0: off) */
+    int filter_passes;
 } osim;
 
 /* ------------------------------------------------------------------ sizes */
@@ -599,6 +601,37 @@ void osim_window(osim *s)
     s->np = keep;
 }
 
+/* --------------------------------------------------------------- current filter
+ * Sec. 4 (nonlinear benchmark): an uncompensated binomial filter of 7 passes is applied
+ * against numerical Cherenkov radiation.  Reading: one pass replaces every value F_i of Jx
+ * and Jr along x by (F_{i-1} + 2 F_i + F_{i+1}) / 4, with F = 0 outside the window; the
+ * charge change dq of the step takes the same passes, so that the filtered current keeps the
+ * continuity equation with the filtered charge.  Radial filtering is not applied.
+ */
+static void binomial_pass_x(double *F, int ni, int nj, double *tmp)
+{
+    memcpy(tmp, F, (size_t)ni * nj * sizeof(double));
+    for (int i = 0; i < ni; i++)
+        for (int j = 0; j < nj; j++) {
+            double left = i > 0 ? tmp[(i - 1) * nj + j] : 0.0;
+            double right = i < ni - 1 ? tmp[(i + 1) * nj + j] : 0.0;
+            F[i * nj + j] = 0.25 * left + 0.5 * tmp[i * nj + j] + 0.25 * right;
+        }
+}
+
+void osim_set_filter(osim *s, int passes) { s->filter_passes = passes > 0 ? passes : 0; }
+
+void osim_filter(osim *s)
+{
+    double *tmp = (double *)malloc((size_t)n_node(s) * sizeof(double));
+    for (int p = 0; p < s->filter_passes; p++) {
+        binomial_pass_x(s->jx, s->nx, s->nr + 1, tmp);
+        binomial_pass_x(s->jr, s->nx + 1, s->nr, tmp);
+        binomial_pass_x(s->dq, s->nx + 1, s->nr + 1, tmp);
+    }
+    free(tmp);
+}
+
 /* One full timestep in the order of the 3D envelope loop the paper follows (Sec. 3). */
 void osim_step(osim *s)
 {
@@ -606,6 +639,7 @@ void osim_step(osim *s)
     osim_pass_a(s);
     osim_envelope(s);
     osim_pass_b(s);
+    if (s->filter_passes > 0) osim_filter(s);
     osim_ampere(s);
     osim_window(s);
 }

@@ -52,8 +52,9 @@ def lib():
             L.osim_free.argtypes = [vp]
             L.osim_init_envelope.argtypes = [vp, d, d, d, d, d]
             L.osim_load_plasma.argtypes = [vp, d, d, d, i, i, i, u64]
+            L.osim_set_filter.argtypes = [vp, i]
             for f in ("osim_step", "osim_faraday", "osim_pass_a", "osim_envelope",
-                      "osim_pass_b", "osim_ampere", "osim_window"):
+                      "osim_pass_b", "osim_ampere", "osim_window", "osim_filter"):
                 getattr(L, f).argtypes = [vp]
             L.osim_run.argtypes = [vp, l]
             L.osim_field.restype = vp
@@ -107,6 +108,11 @@ class OSim:
     def pass_b(self): self.L.osim_pass_b(self.h)
     def ampere(self): self.L.osim_ampere(self.h)
     def window(self): self.L.osim_window(self.h)
+    def filter(self): self.L.osim_filter(self.h)
+
+    def set_filter(self, passes: int):
+        """Binomial current filter of `passes` passes along x after each deposit (0: off)."""
+        self.L.osim_set_filter(self.h, int(passes))
 
     # -- state views -----------------------------------------------------------
     def _shape(self, name):
