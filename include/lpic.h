@@ -69,6 +69,10 @@ typedef struct {
     int64_t particle_capacity;   /* particle slots; lpic_particle_capacity() gives a value  */
     int32_t track_continuity;    /* 1: also deposit the per-step charge change (diagnostic) */
     double accel_px_min;         /* p_x threshold of "accelerated" electrons; <= 0 means 10 */
+    int32_t filter_passes;       /* binomial current filter after each deposit (Sec. 4 nonlinear
+                                    run: 7 passes): each pass replaces Jx, Jr (and the tracked
+                                    charge change) by (F_{i-1} + 2F_i + F_{i+1})/4 along x, zero
+                                    outside the window; 0 = off, at most 16                   */
 } lpic_grid_params;
 
 /* Gaussian envelope (paper Sec. 4; paraxial focused pulse, field profile exp(-xi^2/L^2)). */

@@ -49,6 +49,10 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
         msgf(msg, cap, "particle_capacity=%g out of range", (double)g->particle_capacity);
         return LPIC_EINVAL;
     }
+    if (g->filter_passes < 0 || g->filter_passes > kFilterMaxPasses) {
+        msgf(msg, cap, "filter_passes=%g outside [0, %g]", g->filter_passes, kFilterMaxPasses);
+        return LPIC_EINVAL;
+    }
     if (g->particle_capacity > 0 && g->sort_every < 1) {
         msgf(msg, cap, "sort_every must be >= 1 when particles are present");
         return LPIC_EINVAL;
@@ -87,7 +91,7 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
 }
 
 struct Layout {
-    size_t desc, tab, grid[14], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
+    size_t desc, tab, grid[17], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
     int P, nlive, ncol;
 };
 
@@ -108,6 +112,8 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
     L.grid[6] = L.grid[7] = 0;
     for (int k = 8; k < 10; k++) L.grid[k] = take(cells * 2 * rs);
     for (int k = 10; k < 14; k++) L.grid[k] = take(cells * 8);
+    // filtered current and charge change (only with the binomial filter on)
+    for (int k = 14; k < 17; k++) L.grid[k] = g->filter_passes > 0 ? take(cells * 8) : 0;
     const size_t cap = (size_t)g->particle_capacity;
     for (int b = 0; b < 2; b++) {
         L.parts[b][0] = take(cap * 4);                          // ix
@@ -217,7 +223,7 @@ struct lpic_ctx {
     std::string err;
     bool envelope_set = false;
     // tracing
-    static constexpr int kFamilies = 8;
+    static constexpr int kFamilies = 9;
     long long launches[kFamilies] = {};
     double ms[kFamilies] = {};
     bool timing = false;
@@ -244,8 +250,8 @@ struct lpic_ctx {
 namespace {
 
 const char *const kFamilyNames[lpic_ctx::kFamilies] = {
-    "prepass", "pass_a", "envelope", "pass_b", "ampere", "window", "sort", "relocate"};
-enum Fam { F_PREPASS, F_PASS_A, F_ENVELOPE, F_PASS_B, F_AMPERE, F_WINDOW, F_SORT, F_RELOCATE };
+    "prepass", "pass_a", "envelope", "pass_b", "ampere", "window", "sort", "relocate", "filter"};
+enum Fam { F_PREPASS, F_PASS_A, F_ENVELOPE, F_PASS_B, F_AMPERE, F_WINDOW, F_SORT, F_RELOCATE, F_FILTER };
 constexpr int kSortLaunches = 6;  // memset-free launches of one counting sort
 
 cudaEvent_t pool_event(lpic_ctx *c) {
@@ -290,6 +296,10 @@ template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
     S.f.jx = (double *)(b + L.grid[11]);
     S.f.jr = (double *)(b + L.grid[12]);
     S.f.dq = (double *)(b + L.grid[13]);
+    const bool filt = c->ph.filter_passes > 0;
+    S.f.jxu = filt ? (double *)(b + L.grid[14]) : S.f.jx;
+    S.f.jru = filt ? (double *)(b + L.grid[15]) : S.f.jr;
+    S.f.dqu = filt ? (double *)(b + L.grid[16]) : S.f.dq;
     for (int k = 0; k < 2; k++) {
         S.p[k].ix = (int32_t *)(b + L.parts[k][0]);
         S.p[k].ox = (R *)(b + L.parts[k][1]);
@@ -356,6 +366,7 @@ void enqueue_step_kernels(lpic_ctx *c, const S_ &S, int npl, int inj, cudaStream
     if (npl > 0) traced(c, F_PASS_A, 1, st, [&] { launch_pass_a(S, npl, st); });
     traced(c, F_ENVELOPE, 1, st, [&] { launch_envelope(S, st); });
     if (npl > 0) traced(c, F_PASS_B, 1, st, [&] { launch_pass_b(S, npl, st); });
+    if (S.ph.filter_passes > 0) traced(c, F_FILTER, 1, st, [&] { launch_filter(S, st); });
     traced(c, F_AMPERE, 1, st, [&] { launch_ampere(S, st); });
     traced(c, F_WINDOW, 1, st, [&] { launch_window(S, inj, st); });
 }
@@ -460,6 +471,7 @@ lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_preci
     c->ph.moving_window = g->moving_window ? 1 : 0;
     c->ph.cap = (int)g->particle_capacity;
     c->ph.track_dq = g->track_continuity ? 1 : 0;
+    c->ph.filter_passes = g->filter_passes;
     c->d_desc = (Desc *)(c->buf + L.desc);
     c->key = (int *)(c->buf + L.key);
     c->count = (int *)(c->buf + L.count);
@@ -842,9 +854,9 @@ const char *lpic_last_error(const lpic_ctx *c) {
 
 namespace {
 // work lists: prepass, pass A (and the sort's count and scatter), envelope, pass B, pass B
-// (dq), ampere, window, sort counter blocks, one item per simulation
-constexpr int kBatchLists = 9;
-enum { BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_AMPERE, BL_WINDOW, BL_SORTBLK, BL_SIMS };
+// (dq), ampere, window, sort counter blocks, one item per simulation, current filter
+constexpr int kBatchLists = 10;
+enum { BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_AMPERE, BL_WINDOW, BL_SORTBLK, BL_SIMS, BL_FILTER };
 constexpr int kDefaultChunk = 4096, kMinChunk = 1024, kMaxChunk = 1 << 20;
 
 int window_work(const lpic_ctx *c) {
@@ -868,6 +880,11 @@ size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
         items += (size_t)window_parts(ctxs[k]->geo, window_work(ctxs[k]));
         items += 2 * (size_t)((ctxs[k]->g.particle_capacity + kMinChunk - 1) / kMinChunk);
         items += (size_t)sort_blocks(ctxs[k]->geo) + 1;
+        if (ctxs[k]->ph.filter_passes > 0) {
+            int tx, ty;
+            grid_tiles(ctxs[k]->geo, 3, tx, ty);
+            items += (size_t)tx * ty;
+        }
     }
     return items;
 }
@@ -927,6 +944,12 @@ void plan_pack(const lpic_batch *b, const std::vector<int> &sims, std::vector<in
             for (int by = 0; by < ty; by++)
                 for (int bx = 0; bx < tx; bx++)
                     L[grid_list[ph]].push_back(make_int4(slot, bx, by, ph == 1 && bx == tx - 1 ? 1 : 0));
+        }
+        if (c->ph.filter_passes > 0) {
+            int tx, ty;
+            grid_tiles(c->geo, 3, tx, ty);
+            for (int by = 0; by < ty; by++)
+                for (int bx = 0; bx < tx; bx++) L[BL_FILTER].push_back(make_int4(slot, bx, by, 0));
         }
         const int parts = window_parts(c->geo, window_work(c));
         for (int v = 0; v < parts; v++) L[BL_WINDOW].push_back(make_int4(slot, v, parts, 0));
@@ -1003,13 +1026,14 @@ template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<ch
             for (size_t q = 0; q < packs[p].size(); q++) pk->v[q] = view_of<R>(b->ctx[packs[p][q]]);
             const auto &cn = count[p];
             auto it = [&](int q) { return (const int4 *)(b->items + start[p][q]); };
-            for (int q : {BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_AMPERE, BL_WINDOW})
+            for (int q : {BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_FILTER, BL_AMPERE, BL_WINDOW})
                 nl += cn[q] > 0;
             launch_grid_multi<R>(0, *pk, it(BL_PREPASS), cn[BL_PREPASS], st);
             launch_particles_multi<R>(0, false, *pk, it(BL_SLOTS), cn[BL_SLOTS], st);
             launch_grid_multi<R>(1, *pk, it(BL_ENVELOPE), cn[BL_ENVELOPE], st);
             launch_particles_multi<R>(1, false, *pk, it(BL_PASSB), cn[BL_PASSB], st);
             launch_particles_multi<R>(1, true, *pk, it(BL_PASSB_DQ), cn[BL_PASSB_DQ], st);
+            launch_grid_multi<R>(3, *pk, it(BL_FILTER), cn[BL_FILTER], st);
             launch_grid_multi<R>(2, *pk, it(BL_AMPERE), cn[BL_AMPERE], st);
             launch_window_multi<R>(*pk, it(BL_WINDOW), cn[BL_WINDOW], st);
             if (g == 1 && cn[BL_SIMS] > 0) {

@@ -60,17 +60,20 @@ template <class R> __global__ void k_cont(SimDev<R> S, double *out) {
     const Geo g = S.geo;
     const int off = S.d->off - S.d->last_shift;  // the window the last step deposited on
     const double dx = S.ph.dx, dr = S.ph.dr, dt = S.ph.dt;
-    const long long n = (long long)(g.nx - 1) * g.nr;
+    // interior columns; with the current filter, also away from the `passes` columns at each
+    // end, where filtering on the window only (zero outside) breaks the discrete continuity
+    const int edge = 1 + S.ph.filter_passes;
+    const long long n = (long long)(g.nx + 1 - 2 * edge) * g.nr;
     double rmax = 0.0, dmax = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = 1 + (int)(t / g.nr), j = (int)(t % g.nr);
+        const int i = edge + (int)(t / g.nr), j = (int)(t % g.nr);
         const double ax = j == 0 ? kPi * 0.25 * dr * dr : 2.0 * kPi * j * dr * dr;
-        const double ixp = S.f.jx[g.at(off, i, j)] * ax, ixm = S.f.jx[g.at(off, i - 1, j)] * ax;
-        const double irp = S.f.jr[g.at(off, i, j)] * 2.0 * kPi * (j + 0.5) * dr * dx;
-        const double irm = j == 0 ? 0.0 : S.f.jr[g.at(off, i, j - 1)] * 2.0 * kPi * (j - 0.5) * dr * dx;
+        const double ixp = S.f.jxu[g.at(off, i, j)] * ax, ixm = S.f.jxu[g.at(off, i - 1, j)] * ax;
+        const double irp = S.f.jru[g.at(off, i, j)] * 2.0 * kPi * (j + 0.5) * dr * dx;
+        const double irm = j == 0 ? 0.0 : S.f.jru[g.at(off, i, j - 1)] * 2.0 * kPi * (j - 0.5) * dr * dx;
         const double div = (ixp - ixm) + (irp - irm);
-        const double res = S.f.dq[g.at(off, i, j)] / dt + div;
+        const double res = S.f.dqu[g.at(off, i, j)] / dt + div;
         rmax = fmax(rmax, fabs(res));
         dmax = fmax(dmax, fabs(div));
     }
@@ -146,9 +149,9 @@ template <class R> __global__ void k_dump_field(SimDev<R> S, int kind, int c0, i
             break;
         }
         case 15: st[t] = S.f.chi[id]; break;
-        case 16: st[t] = S.f.jx[id]; break;
-        case 17: st[t] = S.f.jr[id]; break;
-        case 18: st[t] = S.f.dq[id]; break;
+        case 16: st[t] = S.f.jxu[id]; break;
+        case 17: st[t] = S.f.jru[id]; break;
+        case 18: st[t] = S.f.dqu[id]; break;
         }
     }
 }

@@ -174,7 +174,7 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.er[id] = (R)0;
         } else {
             R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * S.k.idx;
-            S.f.er[id] += dt * (-dbdx - from_acc<R>(S.f.jr[id]));
+            S.f.er[id] += dt * (-dbdx - from_acc<R>(S.f.jru[id]));
         }
     }
     if (i < g.nx) {
@@ -182,15 +182,76 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.ex[id] = (R)0;
         } else if (j == 0) {  // axis row in FP64
             double curl = S.k.d_4idr * (double)S.f.bt[id];
-            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jx[id]));
+            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jxu[id]));
         } else {
             R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
-            S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jx[id]));
+            S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jxu[id]));
         }
     }
 }
 
 template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, blockIdx.x, blockIdx.y); }
+
+// Binomial current filter (Sec. 4: an uncompensated binomial filter of 7 passes against
+// numerical Cherenkov radiation): each pass replaces F_i by (F_{i-1} + 2 F_i + F_{i+1})/4 along x,
+// F = 0 outside the window, on Jx, Jr and, when tracked, the charge change dQ (so that the
+// filtered current keeps continuity with the filtered charge); working precision.  Tile
+// (bx, by): rows j = bx*BX + tx, interior columns [by*FX, by*FX + FX).  The tile also holds
+// `passes` halo columns on each side; their values go stale one column per pass, which never
+// reaches the interior.  Tiles read the deposit arrays and write separate ones, so no tile
+// reads a neighbour's output.
+constexpr int FX = 64;
+template <class R>
+__device__ __forceinline__ void filter_array(const double *F, double *out, const Geo &g, int off, int ni, int nj,
+                                             int i0, int j, int passes, R (*t)[BX]) {
+    const int tx = threadIdx.x, ty = threadIdx.y, W = FX + 2 * passes;
+    for (int c = ty; c < W; c += BY) {
+        const int i = i0 - passes + c;
+        t[c][tx] = (i >= 0 && i < ni && j < nj) ? from_acc<R>(F[g.at(off, i, j)]) : (R)0;
+    }
+    __syncthreads();
+    constexpr int NC = (FX + 2 * kFilterMaxPasses + BY - 1) / BY;
+    for (int p = 0; p < passes; p++) {
+        R nv[NC];
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+            const int c = ty + q * BY, i = i0 - passes + c;
+            R v = (R)0;
+            if (c < W && i >= 0 && i < ni) {
+                const R l = c > 0 ? t[c - 1][tx] : (R)0;
+                const R r = c < W - 1 ? t[c + 1][tx] : (R)0;
+                v = (R)0.25 * l + (R)0.5 * t[c][tx] + (R)0.25 * r;
+            }
+            nv[q] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+            const int c = ty + q * BY;
+            if (c < W) t[c][tx] = nv[q];
+        }
+        __syncthreads();
+    }
+    for (int c = passes + ty; c < passes + FX; c += BY) {
+        const int i = i0 - passes + c;
+        if (i < ni && j < nj) out[g.at(off, i, j)] = to_acc(t[c][tx]);
+    }
+    __syncthreads();   // the tile is reused by the next array
+}
+
+template <class R> __device__ __forceinline__ void filter_tile(const SimDev<R> &S, int bx, int by) {
+    __shared__ R t[FX + 2 * kFilterMaxPasses][BX];
+    const Geo g = S.geo;
+    const int off = S.d->off, passes = S.ph.filter_passes;
+    const int j = bx * BX + threadIdx.x, i0 = by * FX;
+    filter_array<R>(S.f.jx, S.f.jxu, g, off, g.nx, g.nr + 1, i0, j, passes, t);
+    filter_array<R>(S.f.jr, S.f.jru, g, off, g.nx + 1, g.nr, i0, j, passes, t);
+    if (S.ph.track_dq) filter_array<R>(S.f.dq, S.f.dqu, g, off, g.nx + 1, g.nr + 1, i0, j, passes, t);
+}
+
+template <class R> __global__ void __launch_bounds__(BX * BY) k_filter(SimDev<R> S) {
+    filter_tile<R>(S, blockIdx.x, blockIdx.y);
+}
 
 // Fused forms over a batch: each block walks work items {simulation, bx, by, flag}.
 template <class R>
@@ -212,6 +273,13 @@ __global__ void __launch_bounds__(BX * BY) k_ampere_multi(const __grid_constant_
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
         ampere_tile<R>(pk.v[it.x], it.y, it.z);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(BX * BY) k_filter_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int4 it = items[w];
+        filter_tile<R>(pk.v[it.x], it.y, it.z);
     }
 }
 
@@ -278,6 +346,11 @@ template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st) {
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st) {
     k_ampere<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);
 }
+template <class R> void launch_filter(const SimDev<R> &S, cudaStream_t st) {
+    int tx, ty;
+    grid_tiles(S.geo, 3, tx, ty);
+    if (S.ph.filter_passes > 0) k_filter<R><<<dim3(tx, ty), dim3(BX, BY), 0, st>>>(S);
+}
 template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
                                             double xc, double xf, cudaStream_t st) {
     k_init_envelope<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S, a0, w0, L,
@@ -294,7 +367,8 @@ template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStr
 void grid_tiles(const Geo &g, int phase, int &tx, int &ty) {
     if (phase == 0) { tx = (g.P + BX - 1) / BX; ty = (g.nlive + BY - 1) / BY; }          // prepass
     else if (phase == 1) { tx = (g.nr + BX - 1) / BX + 1; ty = (g.nx + 1 + BY - 1) / BY; } // envelope
-    else { tx = (g.nr + 1 + BX - 1) / BX; ty = (g.nx + 1 + BY - 1) / BY; }               // ampere
+    else if (phase == 2) { tx = (g.nr + 1 + BX - 1) / BX; ty = (g.nx + 1 + BY - 1) / BY; } // ampere
+    else { tx = (g.nr + 1 + BX - 1) / BX; ty = (g.nx + 1 + FX - 1) / FX; }                 // filter
 }
 
 template <class K> int resident(K *kernel, int threads) {
@@ -308,7 +382,7 @@ template <class K> int resident(K *kernel, int threads) {
 template <class R>
 void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st) {
     if (n <= 0) return;
-    static int res[3] = {0, 0, 0};
+    static int res[4] = {0, 0, 0, 0};
     const dim3 blk(BX, BY);
     if (phase == 0) {
         if (!res[0]) res[0] = resident(k_prepass_multi<R>, BX * BY);
@@ -316,9 +390,12 @@ void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n
     } else if (phase == 1) {
         if (!res[1]) res[1] = resident(k_envelope_multi<R>, BX * BY);
         k_envelope_multi<R><<<n < res[1] ? n : res[1], blk, 0, st>>>(pk, items, n);
-    } else {
+    } else if (phase == 2) {
         if (!res[2]) res[2] = resident(k_ampere_multi<R>, BX * BY);
         k_ampere_multi<R><<<n < res[2] ? n : res[2], blk, 0, st>>>(pk, items, n);
+    } else {
+        if (!res[3]) res[3] = resident(k_filter_multi<R>, BX * BY);
+        k_filter_multi<R><<<n < res[3] ? n : res[3], blk, 0, st>>>(pk, items, n);
     }
 }
 
@@ -327,6 +404,7 @@ void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n
     template void launch_prepass<R>(const SimDev<R> &, cudaStream_t);                        \
     template void launch_envelope<R>(const SimDev<R> &, cudaStream_t);                       \
     template void launch_ampere<R>(const SimDev<R> &, cudaStream_t);                         \
+    template void launch_filter<R>(const SimDev<R> &, cudaStream_t);                         \
     template void launch_init_envelope<R>(const SimDev<R> &, double, double, double, double, \
                                           double, cudaStream_t);                             \
     template void launch_relocate<R>(const SimDev<R> &, int, cudaStream_t);

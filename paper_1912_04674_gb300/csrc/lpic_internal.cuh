@@ -64,7 +64,10 @@ template <class R> struct Fields {
     typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
     R *btn, *phih;                   // per step: B^n, Phi^{n+1/2}
     Q4<R> *pg;                       // per step: (Phi^n, dPhi/dx, dPhi/dr)
-    double *chi, *jx, *jr, *dq;      // per step FP64 accumulators
+    double *chi, *jx, *jr, *dq;      // per step FP64 accumulators (deposit targets)
+    // the current (and charge change) the fields see: the deposit targets, or, with the
+    // binomial filter on, separate arrays the filter writes from them
+    double *jxu, *jru, *dqu;
 };
 
 template <class R> struct Parts {
@@ -82,6 +85,7 @@ struct Phys {
     unsigned long long seed;
     int cap;
     int track_dq;
+    int filter_passes;   // binomial current filter passes after the deposit (0: off)
     // host-computed reciprocals for the lattice generator
     double inv_ramp, inv_ppcx, inv_ppcr, inv_ppct, wfac;  // wfac = 2 pi dr dx / ppc
 };
@@ -152,9 +156,24 @@ __device__ __forceinline__ float d2f_bits(double x) {
     const unsigned bits = special ? nan_or_inf : (e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : fin));
     return __uint_as_float(sgn | bits);
 }
+// FP32 -> FP64 from the IEEE-754 field layouts with integer operations (the FP64 pipe is
+// slow on this part): exponent rebiased by 1023 - 127 = 896, mantissa widened.  FP32
+// subnormals (< 1.2e-38) become 0; infinities and NaNs stay what they are.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x), sgn = u & 0x80000000u, m = u & 0x7fffffffu;
+    const bool tiny = m < 0x00800000u, special = m >= 0x7f800000u;
+    const unsigned hi_n = sgn | ((m >> 3) + (896u << 20));
+    const unsigned hi_s = sgn | 0x7ff00000u | ((m & 0x007fffffu) >> 3);
+    const unsigned hi = tiny ? sgn : (special ? hi_s : hi_n);
+    const unsigned lo = tiny ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 template <class R> __device__ __forceinline__ R from_acc(double x);
 template <> __device__ __forceinline__ float from_acc<float>(double x) { return d2f_bits(x); }
 template <> __device__ __forceinline__ double from_acc<double>(double x) { return x; }
+__device__ __forceinline__ double to_acc(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_acc(double x) { return x; }
 
 template <class R> __device__ __forceinline__ int floor_int(R x);
 template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
@@ -260,6 +279,8 @@ template <class R> void launch_pass_a(const SimDev<R> &S, int np_upper, cudaStre
 template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st);
 template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st);
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st);
+template <class R> void launch_filter(const SimDev<R> &S, cudaStream_t st);
+constexpr int kFilterMaxPasses = 16;
 template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st);
 
 template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
@@ -278,7 +299,8 @@ template <class R> struct SimPack { SimDev<R> v[kPackMax]; };
 static_assert(sizeof(SimPack<double>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764 &&
                   sizeof(SimPack<float>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764,
               "a pack of views must fit the kernel parameter space");
-// grid phases 0 prepass, 1 envelope (c = axis tile), 2 ampere: items {sim, bx, by, c}
+// grid phases 0 prepass, 1 envelope (c = axis tile), 2 ampere, 3 current filter: items
+// {sim, bx, by, c}
 void grid_tiles(const Geo &g, int phase, int &tx, int &ty);
 template <class R>
 void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);

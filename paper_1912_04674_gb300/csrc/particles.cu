@@ -60,19 +60,6 @@ __device__ __forceinline__ R gather4(const R *__restrict__ F, const Geo &geo, in
 
 
 
-// FP32 -> FP64 from the IEEE-754 field layouts with integer operations (the FP64 pipe is
-// slow on this part): exponent rebiased by 1023 - 127 = 896, mantissa widened.  FP32
-// subnormals (< 1.2e-38) become 0; infinities and NaNs stay what they are.
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned u = __float_as_uint(x), sgn = u & 0x80000000u, m = u & 0x7fffffffu;
-    const bool tiny = m < 0x00800000u, special = m >= 0x7f800000u;
-    const unsigned hi_n = sgn | ((m >> 3) + (896u << 20));
-    const unsigned hi_s = sgn | 0x7ff00000u | ((m & 0x007fffffu) >> 3);
-    const unsigned hi = tiny ? sgn : (special ? hi_s : hi_n);
-    const unsigned lo = tiny ? 0u : (m << 29);
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 __device__ __forceinline__ void atom_add(double *p, double v) {
     if (v != 0.0) atomicAdd(p, v);
 }

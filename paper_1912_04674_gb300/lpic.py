@@ -42,7 +42,7 @@ class lpic_grid_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("nr", C.c_int32), ("dx", C.c_double), ("dr", C.c_double),
                 ("dt", C.c_double), ("moving_window", C.c_int32), ("sort_every", C.c_int32),
                 ("particle_capacity", C.c_int64), ("track_continuity", C.c_int32),
-                ("accel_px_min", C.c_double)]
+                ("accel_px_min", C.c_double), ("filter_passes", C.c_int32)]
 
 
 class lpic_laser_params(C.Structure):
@@ -291,6 +291,7 @@ class Grid:
     sort_every: int = 20
     track_continuity: bool = False
     accel_px_min: float = 0.0
+    filter_passes: int = 0
 
 
 @dataclass
@@ -313,7 +314,7 @@ class Plasma:
 
 def grid_struct(g: Grid, plasma: Plasma | None = None, capacity: int | None = None) -> lpic_grid_params:
     s = lpic_grid_params(g.nx, g.nr, g.dx, g.dr, g.dt, int(g.moving_window), int(g.sort_every), 0,
-                         int(g.track_continuity), float(g.accel_px_min))
+                         int(g.track_continuity), float(g.accel_px_min), int(g.filter_passes))
     if capacity is not None:
         s.particle_capacity = int(capacity)
     elif plasma is not None:

@@ -11,8 +11,10 @@ FIELDS = ("ex", "er", "bt", "a", "am", "chi", "jx", "jr")
 PCOMP = ("x", "y", "z", "px", "py", "pz", "w")
 
 
-def oracle_from(w, plasma=True, laser=True, moving=None):
+def oracle_from(w, plasma=True, laser=True, moving=None, filter_passes=0):
     s = OSim(w.nx, w.nr, w.dx, w.dr, w.dt, w.moving_window if moving is None else moving)
+    if filter_passes:
+        s.set_filter(filter_passes)
     if laser:
         s.init_envelope(w.a0, w.w0, w.L, w.x_center, w.x_center)
     if plasma:
@@ -21,10 +23,10 @@ def oracle_from(w, plasma=True, laser=True, moving=None):
 
 
 def gpu_from(w, precision="fp64", plasma=True, laser=True, moving=None, sort_every=None,
-             track=False, capacity=None):
+             track=False, capacity=None, filter_passes=0):
     from paper_1912_04674_gb300 import lpic as L
     g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, w.moving_window if moving is None else moving,
-               sort_every or w.sort_every, track_continuity=track)
+               sort_every or w.sort_every, track_continuity=track, filter_passes=filter_passes)
     la = L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center) if laser else None
     pl = L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed) if plasma else None
     if not plasma and capacity is None:

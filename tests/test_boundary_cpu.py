@@ -41,15 +41,15 @@ def test_library_exports_every_declared_symbol(L):
 def test_struct_layout_matches_c(L, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include "lpic.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
-                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(lpic_grid_params), sizeof(lpic_laser_params),'
+                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lpic_grid_params), sizeof(lpic_laser_params),'
                    'sizeof(lpic_plasma_params), offsetof(lpic_grid_params, particle_capacity),'
-                   'offsetof(lpic_plasma_params, seed));return 0;}\n')
+                   'offsetof(lpic_plasma_params, seed), offsetof(lpic_grid_params, filter_passes));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(L.lpic_grid_params), C.sizeof(L.lpic_laser_params),
                    C.sizeof(L.lpic_plasma_params), L.lpic_grid_params.particle_capacity.offset,
-                   L.lpic_plasma_params.seed.offset]
+                   L.lpic_plasma_params.seed.offset, L.lpic_grid_params.filter_passes.offset]
 
 
 def paper_cases():
@@ -82,7 +82,9 @@ def test_unstable_steps_are_rejected(L):
 
 def test_invalid_arguments_are_rejected(L):
     for g in (L.Grid(1, 32, 0.7, 1.5, 0.5), L.Grid(64, 32, -0.7, 1.5, 0.5),
-              L.Grid(64, 32, 0.7, float("nan"), 0.5)):
+              L.Grid(64, 32, 0.7, float("nan"), 0.5),
+              L.Grid(64, 32, 0.69, 1.5, 0.552, filter_passes=-1),
+              L.Grid(64, 32, 0.69, 1.5, 0.552, filter_passes=17)):
         with pytest.raises(L.LpicError) as e:
             L.lpic_check_params(L.grid_struct(g))
         assert e.value.status == 1
