@@ -384,6 +384,37 @@ def batched_scan(n_sims: int, steps: int, warmup: int = 5):
                         "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc, FP32_MIXED, early steps"}
 
 
+def filter_leg(steps: int = 200, settle_steps: int = 300, passes: int = 7):
+    """C2 FP32_MIXED with the binomial current filter of the nonlinear benchmark (7 passes)
+    against the same run unfiltered, from step `settle_steps`; the filter kernel's time and
+    its HBM roofline (per pass-set: read and write of Jx and Jr in FP64)."""
+    import torch
+
+    from paper_1912_04674_gb300 import lpic as L
+    w = WORKLOAD
+    out = {"workload": w.name, "passes": passes, "from_step": settle_steps, "steps": steps}
+    for label, fp in (("unfiltered", 0), ("filtered", passes)):
+        g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every, filter_passes=fp)
+        sim = L.Simulation(g, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
+                           L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), precision="fp32")
+        settle(sim, settle_steps)
+        ms, alive = timed_steps(sim, steps)
+        out[label] = {"ms_per_step": ms / steps, "value": alive * steps / (ms * 1e-3)}
+        if fp:
+            prof = kernel_profile(sim, 40)
+            t = prof["filter"]["ms_avg"]
+            nbytes = 16 * (w.nx * (w.nr + 1) + (w.nx + 1) * w.nr)
+            pk = peaks().get("hbm_gbs")
+            out["filter_kernel"] = {"ms_per_launch": round(t, 4), "algorithmic_bytes": nbytes,
+                                    "achieved_gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
+                                    "frac_of_measured_hbm": round(nbytes / (t * 1e-3) / 1e9 / pk, 4) if pk else None}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    out["cost_per_step_ms"] = out["filtered"]["ms_per_step"] - out["unfiltered"]["ms_per_step"]
+    return out
+
+
 def large_run(steps: int = 30, warmup: int = 20):
     """The large single run (8192 x 512 cells, 67,108,864 electrons) in both precisions:
     early steps (the pulse already sits in the plasma that fills the initial window)."""
@@ -493,6 +524,7 @@ def run_ours(args):
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
     batch = batched_scan(args.batch_sims, args.batch_steps) if (extras and args.batch_sims > 0) else None
     large = large_run() if (extras and not args.no_large) else None
+    filt = filter_leg() if extras else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
@@ -517,7 +549,8 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "batch": batch, "scan": scan, "gpu_launches": r32["gpu_launches"],
+            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "filter": filt, "batch": batch,
+            "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -582,7 +615,7 @@ def main():
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
-    ap.add_argument("--only", choices=("batch", "large"), default=None,
+    ap.add_argument("--only", choices=("batch", "large", "filter"), default=None,
                     help="run one leg alone and print its object (a profiling run, not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -597,6 +630,9 @@ def main():
         return
     if args.only == "large":
         print(json.dumps({"profile_run": True, "large_run": large_run()}))
+        return
+    if args.only == "filter":
+        print(json.dumps({"profile_run": True, "filter": filter_leg()}))
         return
     run_ours(args)
 

@@ -883,7 +883,7 @@ size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
         if (ctxs[k]->ph.filter_passes > 0) {
             int tx, ty;
             grid_tiles(ctxs[k]->geo, 3, tx, ty);
-            items += (size_t)tx * ty;
+            items += 3 * (size_t)tx * ty;
         }
     }
     return items;
@@ -948,8 +948,9 @@ void plan_pack(const lpic_batch *b, const std::vector<int> &sims, std::vector<in
         if (c->ph.filter_passes > 0) {
             int tx, ty;
             grid_tiles(c->geo, 3, tx, ty);
-            for (int by = 0; by < ty; by++)
-                for (int bx = 0; bx < tx; bx++) L[BL_FILTER].push_back(make_int4(slot, bx, by, 0));
+            for (int a = 0; a < (c->ph.track_dq ? 3 : 2); a++)   // Jx, Jr, dQ
+                for (int by = 0; by < ty; by++)
+                    for (int bx = 0; bx < tx; bx++) L[BL_FILTER].push_back(make_int4(slot, bx, by, a));
         }
         const int parts = window_parts(c->geo, window_work(c));
         for (int v = 0; v < parts; v++) L[BL_WINDOW].push_back(make_int4(slot, v, parts, 0));

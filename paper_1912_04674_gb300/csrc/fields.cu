@@ -199,8 +199,10 @@ template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, blo
 // (bx, by): rows j = bx*BX + tx, interior columns [by*FX, by*FX + FX).  The tile also holds
 // `passes` halo columns on each side; their values go stale one column per pass, which never
 // reaches the interior.  Tiles read the deposit arrays and write separate ones, so no tile
-// reads a neighbour's output.
-constexpr int FX = 64;
+// reads a neighbour's output.  A tile whose halo lies inside the window applies the composed
+// filter, the convolution with C(2p, k)/4^p, in one sweep; tiles at the window's ends run
+// the passes one by one with the zero-outside rule.
+constexpr int FX = 32;
 template <class R>
 __device__ __forceinline__ void filter_array(const double *F, double *out, const Geo &g, int off, int ni, int nj,
                                              int i0, int j, int passes, R (*t)[BX]) {
@@ -210,6 +212,28 @@ __device__ __forceinline__ void filter_array(const double *F, double *out, const
         t[c][tx] = (i >= 0 && i < ni && j < nj) ? from_acc<R>(F[g.at(off, i, j)]) : (R)0;
     }
     __syncthreads();
+    if (i0 - passes >= 0 && i0 + FX + passes <= ni) {
+        // the tile and its halo lie inside the window: the passes compose to one convolution
+        // with the binomial weights C(2p, k) / 4^p, with no boundary to re-apply between them
+        __shared__ R wk[2 * kFilterMaxPasses + 1];
+        if (tx == 0 && ty == 0) {
+            R v = (R)1;
+            for (int p = 0; p < 2 * passes; p++) v *= (R)0.5;   // 4^-p
+            for (int k = 0; k <= 2 * passes; k++) {
+                wk[k] = v;
+                v = v * (R)(2 * passes - k) / (R)(k + 1);
+            }
+        }
+        __syncthreads();
+        for (int c = passes + ty; c < passes + FX; c += BY) {
+            R acc = (R)0;
+            for (int k = 0; k <= 2 * passes; k++) acc += wk[k] * t[c - passes + k][tx];
+            const int i = i0 - passes + c;
+            if (j < nj) out[g.at(off, i, j)] = to_acc(acc);
+        }
+        __syncthreads();   // the tile is reused by the next call
+        return;
+    }
     constexpr int NC = (FX + 2 * kFilterMaxPasses + BY - 1) / BY;
     for (int p = 0; p < passes; p++) {
         R nv[NC];
@@ -239,18 +263,19 @@ __device__ __forceinline__ void filter_array(const double *F, double *out, const
     __syncthreads();   // the tile is reused by the next array
 }
 
-template <class R> __device__ __forceinline__ void filter_tile(const SimDev<R> &S, int bx, int by) {
+// Array `which` (0 Jx, 1 Jr, 2 dQ) of tile (bx, by).
+template <class R> __device__ __forceinline__ void filter_tile(const SimDev<R> &S, int bx, int by, int which) {
     __shared__ R t[FX + 2 * kFilterMaxPasses][BX];
     const Geo g = S.geo;
     const int off = S.d->off, passes = S.ph.filter_passes;
     const int j = bx * BX + threadIdx.x, i0 = by * FX;
-    filter_array<R>(S.f.jx, S.f.jxu, g, off, g.nx, g.nr + 1, i0, j, passes, t);
-    filter_array<R>(S.f.jr, S.f.jru, g, off, g.nx + 1, g.nr, i0, j, passes, t);
-    if (S.ph.track_dq) filter_array<R>(S.f.dq, S.f.dqu, g, off, g.nx + 1, g.nr + 1, i0, j, passes, t);
+    if (which == 0) filter_array<R>(S.f.jx, S.f.jxu, g, off, g.nx, g.nr + 1, i0, j, passes, t);
+    else if (which == 1) filter_array<R>(S.f.jr, S.f.jru, g, off, g.nx + 1, g.nr, i0, j, passes, t);
+    else if (S.ph.track_dq) filter_array<R>(S.f.dq, S.f.dqu, g, off, g.nx + 1, g.nr + 1, i0, j, passes, t);
 }
 
 template <class R> __global__ void __launch_bounds__(BX * BY) k_filter(SimDev<R> S) {
-    filter_tile<R>(S, blockIdx.x, blockIdx.y);
+    filter_tile<R>(S, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Fused forms over a batch: each block walks work items {simulation, bx, by, flag}.
@@ -279,7 +304,7 @@ template <class R>
 __global__ void __launch_bounds__(BX * BY) k_filter_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        filter_tile<R>(pk.v[it.x], it.y, it.z);
+        filter_tile<R>(pk.v[it.x], it.y, it.z, it.w);
     }
 }
 
@@ -349,7 +374,7 @@ template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st) {
 template <class R> void launch_filter(const SimDev<R> &S, cudaStream_t st) {
     int tx, ty;
     grid_tiles(S.geo, 3, tx, ty);
-    if (S.ph.filter_passes > 0) k_filter<R><<<dim3(tx, ty), dim3(BX, BY), 0, st>>>(S);
+    if (S.ph.filter_passes > 0) k_filter<R><<<dim3(tx, ty, S.ph.track_dq ? 3 : 2), dim3(BX, BY), 0, st>>>(S);
 }
 template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
                                             double xc, double xf, cudaStream_t st) {
