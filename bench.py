@@ -273,6 +273,19 @@ def e2e_run(prec: str, k: int, settle_steps: int):
             "note": "upload of a settled state amortised over the steps; wake read back every step"}
 
 
+def beam_compare(s64, s32, s64b):
+    """Table BeamParams quantities of the injected electrons, FP32 and FP64-reordered against
+    FP64, and the wall time of one beam diagnostic (three kernels and a 256-bin spectrum)."""
+    t0 = time.perf_counter()
+    b64 = s64.beam_parameters()
+    ms = (time.perf_counter() - t0) * 1e3
+    b32, b64b = s32.beam_parameters(), s64b.beam_parameters()
+    keys = ("charge", "e_peak", "fwhm", "de_over_e", "eps_mean")
+    rel = lambda a, b: float(abs(a / b - 1)) if b else None  # noqa: E731
+    return {"fp64": b64, "fp32": b32, "fp32_rel": {k: rel(b32[k], b64[k]) for k in keys},
+            "fp64_reordered_rel": {k: rel(b64b[k], b64[k]) for k in keys}, "diag_ms": round(ms, 3)}
+
+
 def accuracy(k_total: int, horizon: int = 300):
     """FP32_MIXED against FP64 on the same workload, beside the FP64 run-to-run spread.
 
@@ -304,6 +317,7 @@ def accuracy(k_total: int, horizon: int = 300):
                 "fp64_reordered_wake_ex_rel_l2": float(np.linalg.norm(s64b.ex_axis() - e64) / n),
                 "fp64_reordered_a_max_rel": float(abs(s64b.a_abs_max() / a64 - 1)),
                 "continuity_residual": {"fp64": s64.cont_residual(), "fp32": s32.cont_residual()},
+                "beam": beam_compare(s64, s32, s64b),
                 "accelerated_electrons": {"fp64": acc64, "fp32": acc32, "fp64_reordered": acc64b,
                                           "fp32_mean_rel": rel(acc32["mean_gamma_minus_1"], acc64["mean_gamma_minus_1"]),
                                           "fp32_rms_rel": rel(acc32["rms_gamma_minus_1"], acc64["rms_gamma_minus_1"])}}

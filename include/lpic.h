@@ -99,6 +99,17 @@ typedef enum {
     LPIC_DIAG_ACCEL_ENERGY = 4,  /* 4 doubles: count, sum w, weighted mean and rms of gamma-1
                                     over alive electrons with p_x > accel_px_min            */
     LPIC_DIAG_COUNTERS = 5,      /* 4 int64: step n, window shift s, particle slots, alive   */
+    LPIC_DIAG_BEAM = 6,          /* 12 doubles, the injected-beam parameters of Table BeamParams
+                                    (Sec. 4) over alive electrons with p_x > accel_px_min:
+                                    {n_accel, n_beam, charge (sum w), E_peak, FWHM, dE/E,
+                                    eps_y, eps_z, eps_mean, mean E, E_max, bins}.  E = gamma-1
+                                    (m c^2); spectrum = w-weighted histogram of E in 256 bins
+                                    over [0, E_max]; E_peak = centre of the first largest bin;
+                                    FWHM from the half-maximum crossings (linear interpolation
+                                    between bin centres); beam = |E - E_peak| <= FWHM;
+                                    dE/E = rms E over the beam / E_peak; eps_u =
+                                    sqrt(s_uu s_pp - s_up^2) of the beam's central moments
+                                    (c/w0 units), u = y, z.  All zero without accelerated e-. */
     LPIC_DIAG_EX = 10, LPIC_DIAG_ER = 11, LPIC_DIAG_BT = 12,
     LPIC_DIAG_A = 13,            /* A^n, complex (re,im)                                     */
     LPIC_DIAG_AM = 14,           /* A^{n-1}, complex (re,im)                                 */

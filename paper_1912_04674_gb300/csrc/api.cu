@@ -653,6 +653,58 @@ lpic_status lpic_diagnose(lpic_ctx *c, lpic_diag_kind kind, void *host_out, size
         memcpy(host_out, o, sizeof o);
         return LPIC_OK;
     }
+    case LPIC_DIAG_BEAM: {
+        if (!need(12 * sizeof(double))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        const double thr = c->g.accel_px_min > 0 ? c->g.accel_px_min : 10.0;
+        const int npl = launch_cap(c), nb = kBeamBins;
+        double o[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, (double)nb};
+        double mx[2];
+        c->dispatch([&](auto &S) { launch_beam_max(S, npl, thr, c->diag, c->st); });
+        if ((s = copy_back(mx, c->diag, sizeof mx)) != LPIC_OK) return s;
+        o[0] = mx[1];
+        o[10] = mx[0];
+        if (mx[1] > 0) {
+            // spectrum, its peak and half-maximum crossings (host side: nb values)
+            const double width = mx[0] > 0 ? mx[0] / nb : 1.0;
+            std::vector<double> hist(nb);
+            c->dispatch([&](auto &S) { launch_beam_hist(S, npl, thr, width, nb, (double *)c->stage, c->st); });
+            if ((s = copy_back(hist.data(), c->stage, nb * sizeof(double))) != LPIC_OK) return s;
+            int kp = 0;
+            for (int b = 1; b < nb; b++)
+                if (hist[b] > hist[kp]) kp = b;
+            const double half = 0.5 * hist[kp];
+            auto crossing = [&](int step) {
+                int b = kp;
+                while (b + step >= 0 && b + step < nb && hist[b + step] >= half) b += step;
+                const int nx_ = b + step;
+                const double hn = (nx_ >= 0 && nx_ < nb) ? hist[nx_] : 0.0;
+                const double t = hist[b] != hn ? (hist[b] - half) / (hist[b] - hn) : 0.0;
+                return (b + 0.5) * width + step * t * width;
+            };
+            const double e_peak = (kp + 0.5) * width, fwhm = crossing(1) - crossing(-1);
+            o[3] = e_peak;
+            o[4] = fwhm;
+            double m[14];
+            c->dispatch([&](auto &S) { launch_beam_moments(S, npl, thr, e_peak, fwhm, c->diag, c->st); });
+            if ((s = copy_back(m, c->diag, sizeof m)) != LPIC_OK) return s;
+            o[1] = m[13];
+            o[2] = m[0];
+            if (m[0] > 0) {
+                const double q = m[0], em = m[1] / q;
+                o[9] = em;
+                o[5] = std::sqrt(std::fmax(m[2] / q - em * em, 0.0)) / e_peak;
+                for (int u = 0; u < 2; u++) {
+                    const double *a = m + 3 + 5 * u;
+                    const double mu = a[0] / q, mp = a[2] / q;
+                    const double suu = a[1] / q - mu * mu, spp = a[3] / q - mp * mp, sup = a[4] / q - mu * mp;
+                    o[6 + u] = std::sqrt(std::fmax(suu * spp - sup * sup, 0.0));
+                }
+                o[8] = 0.5 * (o[6] + o[7]);
+            }
+        }
+        memcpy(host_out, o, sizeof o);
+        return LPIC_OK;
+    }
     case LPIC_DIAG_COUNTERS: {
         if (!need(4 * sizeof(int64_t))) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
         c->dispatch([&](auto &S) { launch_alive_index(S, launch_cap(c), c->key, c->blockcnt, c->icount, c->st); });

@@ -87,6 +87,72 @@ template <class R> __global__ void k_cont(SimDev<R> S, double *out) {
     }
 }
 
+// ---- beam parameters of the accelerated electrons (Table BeamParams quantities) -----------
+// Energy gamma - 1 of slot k in FP64, without contraction, so that a particle state gives the
+// same bits here and in any other IEEE evaluation of sqrt(1 + px^2 + py^2 + pz^2) - 1.
+template <class R> __device__ __forceinline__ double beam_energy(const Parts<R> &P, int k) {
+    const double px = P.px[k], py = P.py[k], pz = P.pz[k];
+    const double s = __dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(px, px)), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+    return __dsub_rn(sqrt(s), 1.0);
+}
+
+// out = {max energy, count} over alive particles with p_x > thr.
+template <class R> __global__ void k_beam_max(SimDev<R> S, double thr, double *out) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const int np = S.d->np;
+    double m = 0.0, c = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        if (P.ix[k] == kDead || !((double)P.px[k] > thr)) continue;
+        m = fmax(m, beam_energy<R>(P, k));
+        c += 1.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c > 0) {
+        atomic_max_nonneg(out, m);
+        atomicAdd(out + 1, c);
+    }
+}
+
+// w-weighted energy histogram, bins of `width` over [0, nbins*width) (the last bin takes the top).
+template <class R> __global__ void k_beam_hist(SimDev<R> S, double thr, double width, int nbins, double *hist) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const int np = S.d->np;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        if (P.ix[k] == kDead || !((double)P.px[k] > thr)) continue;
+        const double b = floor(__ddiv_rn(beam_energy<R>(P, k), width));
+        atomicAdd(hist + (b < (double)(nbins - 1) ? (int)b : nbins - 1), (double)P.w[k]);
+    }
+}
+
+// Sums over the beam (|E - e_peak| <= fwhm): w, wE, wE^2, then for u = y, z: w u, w u^2, w p_u,
+// w p_u^2, w u p_u; and the count.  out: 14 doubles.
+template <class R>
+__global__ void k_beam_moments(SimDev<R> S, double thr, double e_peak, double fwhm, double *out) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const int np = S.d->np;
+    double a[14];
+#pragma unroll
+    for (int q = 0; q < 14; q++) a[q] = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        if (P.ix[k] == kDead || !((double)P.px[k] > thr)) continue;
+        const double e = beam_energy<R>(P, k);
+        if (!(fabs(e - e_peak) <= fwhm)) continue;
+        const double w = P.w[k], y = P.y[k], z = P.z[k], py = P.py[k], pz = P.pz[k];
+        a[0] += w; a[1] += w * e; a[2] += w * e * e;
+        a[3] += w * y; a[4] += w * y * y; a[5] += w * py; a[6] += w * py * py; a[7] += w * y * py;
+        a[8] += w * z; a[9] += w * z * z; a[10] += w * pz; a[11] += w * pz * pz; a[12] += w * z * pz;
+        a[13] += 1.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 14; q++)
+        for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+    if ((threadIdx.x & 31) == 0 && a[13] > 0)
+        for (int q = 0; q < 14; q++) atomicAdd(out + q, a[q]);
+}
+
 // out = {count, sum w, sum w (g-1), sum w (g-1)^2} over alive particles with p_x > thr.
 template <class R> __global__ void k_accel(SimDev<R> S, double thr, double *out) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
@@ -313,6 +379,23 @@ void launch_diag_accel(const SimDev<R> &S, int np_upper, double thr, double *out
     k_accel<R><<<pgrid(np_upper), TPB, 0, st>>>(S, thr, out4);
 }
 template <class R>
+void launch_beam_max(const SimDev<R> &S, int np_upper, double thr, double *out2, cudaStream_t st) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+    k_beam_max<R><<<pgrid(np_upper), TPB, 0, st>>>(S, thr, out2);
+}
+template <class R>
+void launch_beam_hist(const SimDev<R> &S, int np_upper, double thr, double width, int nbins, double *hist,
+                      cudaStream_t st) {
+    cudaMemsetAsync(hist, 0, nbins * sizeof(double), st);
+    k_beam_hist<R><<<pgrid(np_upper), TPB, 0, st>>>(S, thr, width, nbins, hist);
+}
+template <class R>
+void launch_beam_moments(const SimDev<R> &S, int np_upper, double thr, double e_peak, double fwhm, double *out14,
+                         cudaStream_t st) {
+    cudaMemsetAsync(out14, 0, 14 * sizeof(double), st);
+    k_beam_moments<R><<<pgrid(np_upper), TPB, 0, st>>>(S, thr, e_peak, fwhm, out14);
+}
+template <class R>
 void launch_dump_field(const SimDev<R> &S, int kind, int c0, int c1, double *stage, cudaStream_t st) {
     int ni, nj, cp;
     kind_shape(kind, S.geo.nx, S.geo.nr, ni, nj, cp);
@@ -358,6 +441,11 @@ template <class R> void launch_finish_upload(const SimDev<R> &S, int n, cudaStre
     template void launch_diag_amax_waist<R>(const SimDev<R> &, double *, cudaStream_t);         \
     template void launch_diag_cont<R>(const SimDev<R> &, double *, cudaStream_t);               \
     template void launch_diag_accel<R>(const SimDev<R> &, int, double, double *, cudaStream_t); \
+    template void launch_beam_max<R>(const SimDev<R> &, int, double, double *, cudaStream_t);   \
+    template void launch_beam_hist<R>(const SimDev<R> &, int, double, double, int, double *,    \
+                                      cudaStream_t);                                            \
+    template void launch_beam_moments<R>(const SimDev<R> &, int, double, double, double, double *, \
+                                         cudaStream_t);                                         \
     template void launch_dump_field<R>(const SimDev<R> &, int, int, int, double *, cudaStream_t); \
     template void launch_upload_field<R>(const SimDev<R> &, int, int, int, const double *,      \
                                          cudaStream_t);                                         \

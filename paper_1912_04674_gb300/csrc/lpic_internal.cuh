@@ -334,6 +334,12 @@ template <class R> void launch_sort(const SimDev<R> &S, int np_upper, int *key, 
 template <class R> void launch_diag_ex_axis(const SimDev<R> &S, double *out, cudaStream_t st);
 template <class R> void launch_diag_amax_waist(const SimDev<R> &S, double *out3, cudaStream_t st);
 template <class R> void launch_diag_cont(const SimDev<R> &S, double *out2, cudaStream_t st);
+template <class R> void launch_beam_max(const SimDev<R> &S, int np_upper, double thr, double *out2, cudaStream_t st);
+template <class R> void launch_beam_hist(const SimDev<R> &S, int np_upper, double thr, double width, int nbins,
+                                         double *hist, cudaStream_t st);
+template <class R> void launch_beam_moments(const SimDev<R> &S, int np_upper, double thr, double e_peak,
+                                            double fwhm, double *out14, cudaStream_t st);
+constexpr int kBeamBins = 256;
 template <class R> void launch_diag_accel(const SimDev<R> &S, int np_upper, double thr,
                                           double *out4, cudaStream_t st);
 // canonical dump / upload of one grid array (kind as in lpic_diag_kind), columns [c0, c1)

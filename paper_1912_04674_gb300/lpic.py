@@ -27,7 +27,7 @@ STATUS = {0: "LPIC_OK", 1: "LPIC_EINVAL", 2: "LPIC_ECFL", 3: "LPIC_ENOMEM_BUDGET
 LPIC_FP64, LPIC_FP32_MIXED = 0, 1
 PRECISION = {"fp64": LPIC_FP64, "fp32": LPIC_FP32_MIXED, "fp32_mixed": LPIC_FP32_MIXED}
 DIAG = {"ex_axis": 0, "a_abs_max": 1, "waist": 2, "cont_residual": 3, "accel_energy": 4,
-        "counters": 5, "ex": 10, "er": 11, "bt": 12, "a": 13, "am": 14, "chi": 15, "jx": 16,
+        "counters": 5, "beam": 6, "ex": 10, "er": 11, "bt": 12, "a": 13, "am": 14, "chi": 15, "jx": 16,
         "jr": 17, "dq": 18, "particles": 20, "particle_ids": 21}
 PART_COMPONENTS = ("x", "y", "z", "px", "py", "pz", "w")
 
@@ -398,6 +398,14 @@ class Simulation:
 
     def accel_energy(self) -> np.ndarray:
         return self._diag("accel_energy", np.float64, 4)
+
+    BEAM_FIELDS = ("n_accel", "n_beam", "charge", "e_peak", "fwhm", "de_over_e", "eps_y", "eps_z",
+                   "eps_mean", "e_mean", "e_max", "nbins")
+
+    def beam_parameters(self) -> dict:
+        """Injected-beam parameters of Table BeamParams (see LPIC_DIAG_BEAM)."""
+        v = self._diag("beam", np.float64, 12)
+        return {k: float(x) for k, x in zip(self.BEAM_FIELDS, v)}
 
     def counters(self) -> dict:
         v = self._diag("counters", np.int64, 4)
