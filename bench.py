@@ -429,6 +429,38 @@ def filter_leg(steps: int = 200, settle_steps: int = 300, passes: int = 7):
     return out
 
 
+def bunch_leg(gamma: float = 200.0):
+    """Inject a quiet Gaussian electron bunch (sigma_x = 4, sigma_r = 3 c/w0, 0.05 charge units,
+    behind the laser) into the C2 run in FP32: wall time of lpic_inject_bunch (append, charge,
+    preconditioned CG solve of the discrete Gauss law on the 2049 x 256 nodes, fields)."""
+    import numpy as np
+    import torch
+
+    w = WORKLOAD
+    sim = make_sim("fp32")
+    xc, sx, sr = 0.4 * w.nx * w.dx, 4.0, 3.0
+    xs = np.arange(xc - 4 * sx, xc + 4 * sx, w.dx / 4) + w.dx / 8
+    rs = (np.arange(int(4 * sr / w.dr * 4)) + 0.5) * w.dr / 4
+    th = (np.arange(8) + 0.5) * 2 * np.pi / 8
+    X, Rr, T = np.meshgrid(xs, rs, th, indexing="ij")
+    x, r, t = X.ravel(), Rr.ravel(), T.ravel()
+    wt = np.exp(-(x - xc) ** 2 / (2 * sx * sx) - r * r / (2 * sr * sr)) * r
+    n = len(x)
+    beta = np.sqrt(1 - 1 / gamma**2)
+    parts = dict(x=x, y=r * np.cos(t), z=r * np.sin(t), px=np.full(n, gamma * beta), py=np.zeros(n),
+                 pz=np.zeros(n), w=wt * 0.05 / wt.sum())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.inject_bunch(parts, gamma)
+    ms = (time.perf_counter() - t0) * 1e3
+    er = sim.field("er")
+    sim.step(20)
+    out = {"workload": w.name, "electrons": n, "gamma": gamma, "inject_ms": round(ms, 2),
+           "max_er": float(np.abs(er).max()), "alive_after_20_steps": sim.counters()["alive"]}
+    sim.close()
+    return out
+
+
 def large_run(steps: int = 30, warmup: int = 20):
     """The large single run (8192 x 512 cells, 67,108,864 electrons) in both precisions:
     early steps (the pulse already sits in the plasma that fills the initial window)."""
@@ -539,6 +571,7 @@ def run_ours(args):
     batch = batched_scan(args.batch_sims, args.batch_steps) if (extras and args.batch_sims > 0) else None
     large = large_run() if (extras and not args.no_large) else None
     filt = filter_leg() if extras else None
+    bunch = bunch_leg() if extras else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
@@ -563,7 +596,7 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "filter": filt, "batch": batch,
+            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "filter": filt, "bunch": bunch, "batch": batch,
             "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
@@ -629,7 +662,7 @@ def main():
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
-    ap.add_argument("--only", choices=("batch", "large", "filter"), default=None,
+    ap.add_argument("--only", choices=("batch", "large", "filter", "bunch"), default=None,
                     help="run one leg alone and print its object (a profiling run, not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -647,6 +680,9 @@ def main():
         return
     if args.only == "filter":
         print(json.dumps({"profile_run": True, "filter": filter_leg()}))
+        return
+    if args.only == "bunch":
+        print(json.dumps({"profile_run": True, "bunch": bunch_leg()}))
         return
     run_ours(args)
 

@@ -212,6 +212,22 @@ lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t n
 /* Release the context (host memory only; the device buffer stays the caller's). */
 lpic_status lpic_destroy(lpic_ctx *ctx);
 
+/* ---- externally injected relativistic bunch (Sec. 3: the field initialisation of a bunch
+ * in uniform motion, in cylindrical symmetry) -------------------------------------------------
+ * Appends n electrons (host_parts: 7 x n doubles, SoA as for LPIC_DIAG_PARTICLES: lab x, y,
+ * z, px, py, pz, w; ids 2^63 + a running count) and adds to E^n and B^{n-1/2} the fields of
+ * their charge moving along x at beta = sqrt(1 - 1/gamma^2):
+ *   E = -(dphi/dx / gamma^2, dphi/dr),  B_theta = beta E_r moved back by beta dt/2,
+ * phi from the flux-form discrete Gauss law of the Yee grid (the divergence the Maxwell solver
+ * conserves) with no x flux through the window ends and phi = 0 at r_max, solved by
+ * preconditioned conjugate gradients to a relative residual of 1e-12 (at most 2000
+ * iterations).  scratch: caller-owned device memory of lpic_bunch_scratch_bytes, 256-byte
+ * aligned, free again when the call returns.  Synchronous.  Errors: LPIC_EINVAL (gamma <= 1,
+ * non-finite input, bad scratch), LPIC_EBUFSIZE (capacity), LPIC_ENONFINITE (no convergence). */
+size_t lpic_bunch_scratch_bytes(const lpic_ctx *ctx);
+lpic_status lpic_inject_bunch(lpic_ctx *ctx, const double *host_parts, int64_t n, double gamma, void *scratch,
+                              size_t scratch_bytes);
+
 /* Message of the last failing call on ctx (or of the last failing lpic_init_grid /
  * lpic_batch_create on this thread when ctx is NULL).  Never NULL. */
 const char *lpic_last_error(const lpic_ctx *ctx);

@@ -217,6 +217,7 @@ struct lpic_ctx {
     int off = 0;
     long long np_upper = 0;
     int since_sort = 0;
+    unsigned long long bunch_ids = 0;   // injected-bunch particles so far
     Desc *h_desc = nullptr;          // pinned
     cudaEvent_t ev = nullptr;
     bool ev_pending = false;
@@ -841,6 +842,69 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
     default:
         return c->fail(LPIC_EINVAL, "this kind cannot be uploaded");
     }
+}
+
+size_t lpic_bunch_scratch_bytes(const lpic_ctx *c) { return c ? bunch_scratch_bytes(c->geo) : 0; }
+
+lpic_status lpic_inject_bunch(lpic_ctx *c, const double *host_parts, int64_t n, double gamma, void *scratch,
+                              size_t scratch_bytes) {
+    if (!c) return LPIC_EINVAL;
+    if (!(gamma > 1.0) || !std::isfinite(gamma)) return c->fail(LPIC_EINVAL, "inject_bunch: gamma must be > 1");
+    if (n < 0 || (n > 0 && !host_parts)) return c->fail(LPIC_EINVAL, "inject_bunch: bad particle array");
+    if (!scratch || ((uintptr_t)scratch % 256) != 0 || scratch_bytes < bunch_scratch_bytes(c->geo))
+        return c->fail(LPIC_EINVAL, "inject_bunch: scratch must be 256-byte aligned and hold lpic_bunch_scratch_bytes");
+    for (int64_t k = 0; k < 7 * n; k++)
+        if (!std::isfinite(host_parts[k])) return c->fail(LPIC_EINVAL, "inject_bunch: non-finite particle value");
+    {   // every electron inside the window: x in [s dx, (s + Nx) dx), r < r_max
+        const double x0 = c->shift * c->ph.dx, x1 = (c->shift + c->geo.nx) * c->ph.dx, rmax = c->geo.nr * c->ph.dr;
+        for (int64_t k = 0; k < n; k++) {
+            const double x = host_parts[k], y = host_parts[n + k], z = host_parts[2 * n + k];
+            if (!(x >= x0 && x < x1) || !(std::sqrt(y * y + z * z) < rmax))
+                return c->fail(LPIC_EINVAL, "inject_bunch: an electron lies outside the window");
+        }
+    }
+    lpic_status s = pull_desc(c);
+    if (s != LPIC_OK) return s;
+    const long long np0 = c->h_desc->np;
+    if (np0 + n > c->g.particle_capacity) return c->fail(LPIC_EBUFSIZE, "inject_bunch: particle capacity exceeded");
+    auto h2d = [&](void *dst, const void *src, size_t bytes) -> lpic_status {
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // the stage is reused next
+        return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "inject_bunch");
+    };
+    // append the particles at slots [np0, np0 + n)
+    const int chunk = (int)(c->stage_bytes / 8);
+    for (int comp = 0; comp < 7; comp++)
+        for (long long k0 = 0; k0 < n; k0 += chunk) {
+            const long long k1 = k0 + chunk < n ? k0 + chunk : n;
+            if ((s = h2d(c->stage, host_parts + comp * n + k0, 8 * (size_t)(k1 - k0))) != LPIC_OK) return s;
+            c->dispatch([&](auto &S) { launch_upload_particles(S, (int)(np0 + k0), (int)(np0 + k1), comp, (const double *)c->stage, c->st); });
+        }
+    std::vector<uint64_t> ids;
+    for (long long k0 = 0; k0 < n; k0 += chunk) {
+        const long long k1 = k0 + chunk < n ? k0 + chunk : n;
+        ids.resize(k1 - k0);
+        for (long long t = k0; t < k1; t++) ids[t - k0] = (1ull << 63) + c->bunch_ids + (unsigned long long)t;
+        if ((s = h2d(c->stage, ids.data(), 8 * ids.size())) != LPIC_OK) return s;
+        c->dispatch([&](auto &S) { launch_set_ids(S, nullptr, (int)(np0 + k0), (int)(np0 + k1), (const uint64_t *)c->stage, nullptr, 1, c->st); });
+    }
+    c->bunch_ids += (unsigned long long)n;
+    c->h_desc->np = (int)(np0 + n);
+    c->h_desc->n_alive += (int)n;
+    if ((s = push_desc(c)) != LPIC_OK) return s;
+    c->np_upper = np0 + n > c->np_upper ? np0 + n : c->np_upper;
+    // fields of the bunch
+    int iters = 0;
+    double res = 0.0;
+    c->dispatch([&](auto &S) {
+        iters = bunch_solve_and_add(S, (int)np0, (int)n, gamma, scratch, c->diag, 1e-12, 2000, c->st, &res);
+    });
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return c->cuda_fail(e, "inject_bunch");
+    if (!(res <= 1e-12) || !std::isfinite(res)) return c->fail(LPIC_ENONFINITE, "inject_bunch: the field solve did not converge");
+    (void)iters;
+    return LPIC_OK;
 }
 
 lpic_status lpic_set_kernel_timing(lpic_ctx *c, int enable) {

@@ -289,6 +289,14 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
                                             int total, cudaStream_t st);
 template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
 
+// ---- injected bunch: its charge from particle slots [k0, k0 + n), the discrete Gauss-law solve
+// (preconditioned CG to relative residual tol, at most max_iter iterations) and the addition of
+// its fields to E^n, B^{n-1/2}; returns the iterations, *res the final relative residual.
+size_t bunch_scratch_bytes(const Geo &g);
+template <class R>
+int bunch_solve_and_add(const SimDev<R> &S, int k0, int n, double gamma, void *scratch, double *d_dot, double tol,
+                        int max_iter, cudaStream_t st, double *res_out);
+
 // ---- fused batch forms: one launch per phase over work items {sim, a, b, c} -------------
 // The views of the simulations of one fused launch travel by value in the kernel's
 // parameter space (a __grid_constant__ pack, read through the constant cache like a single

@@ -74,6 +74,8 @@ _SIGS = {
     "lpic_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "lpic_kernel_name": (C.c_char_p, [C.c_int]),
     "lpic_envelope_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
+    "lpic_bunch_scratch_bytes": (C.c_size_t, [C.c_void_p]),
+    "lpic_inject_bunch": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_double, C.c_void_p, C.c_size_t]),
     "lpic_destroy": (C.c_int, [C.c_void_p]),
     "lpic_last_error": (C.c_char_p, [C.c_void_p]),
     "lpic_batch_required_bytes": (C.c_size_t, [C.POINTER(C.c_void_p), C.c_int]),
@@ -188,6 +190,17 @@ def lpic_envelope_stats_noalloc(a_dev_ptr: int, nx: int, nr: int, dr: float, out
                                            C.c_void_p(out_dev_ptr), C.c_void_p(stream_ptr))
     if st != LPIC_OK:
         raise LpicError(st, "lpic_envelope_stats_noalloc failed")
+
+
+def lpic_bunch_scratch_bytes(ctx) -> int:
+    return int(lib().lpic_bunch_scratch_bytes(ctx))
+
+
+def lpic_inject_bunch(ctx, parts7n: np.ndarray, gamma: float, scratch_ptr: int, scratch_bytes: int):
+    a = np.ascontiguousarray(parts7n, dtype=np.float64)
+    n = a.size // 7
+    _check(lib().lpic_inject_bunch(ctx, a.ctypes.data_as(C.POINTER(C.c_double)), n, float(gamma),
+                                   C.c_void_p(scratch_ptr), int(scratch_bytes)), ctx)
 
 
 def lpic_destroy(ctx):
@@ -443,6 +456,20 @@ class Simulation:
         if "id" in parts and n:
             ids = np.ascontiguousarray(parts["id"], dtype=np.uint64)
             lpic_upload(self.ctx, DIAG["particle_ids"], ids.ctypes.data_as(C.c_void_p), ids.nbytes)
+
+    def inject_bunch(self, parts: dict, gamma: float):
+        """Append a relativistic electron bunch (x lab, y, z, px, py, pz, w) and add its
+        self-consistent fields (lpic_inject_bunch); the solver scratch comes from PyTorch."""
+        import torch
+
+        n = len(parts["x"])
+        raw = np.concatenate([np.asarray(parts[k], dtype=np.float64) for k in PART_COMPONENTS]) if n else np.zeros(0)
+        nbytes = lpic_bunch_scratch_bytes(self.ctx)
+        buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        with torch.cuda.device(self.device):
+            lpic_inject_bunch(self.ctx, raw, gamma, ptr, nbytes)
+        del buf
 
     def upload_counters(self, step: int, shift: int):
         v = np.array([step, shift, 0, 0], dtype=np.int64)
