@@ -237,11 +237,20 @@ struct lpic_ctx {
         err = std::string(where) + ": " + cudaGetErrorString(e);
         return LPIC_ECUDA;
     }
+    // one step (and one step followed by the sort) recorded as CUDA graphs, replayed while
+    // kernel timing is off; launches per replay by family
+    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+    long long step_launches[2][9] = {};
+    void drop_step_graphs() {
+        for (auto &e : step_exec)
+            if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    }
     void sync_views() {   // after a change of the physics parameters (plasma loading)
         sd.ph = ph;
         sf.ph = ph;
         sd.k = make_consts<double>(ph, geo.nr, sd.k.tab);
         sf.k = make_consts<float>(ph, geo.nr, sf.k.tab);
+        drop_step_graphs();   // the recorded launches carry the old views
     }
     template <class F> void dispatch(F &&f) {
         if (prec == LPIC_FP64) f(sd); else f(sf);
@@ -577,6 +586,32 @@ lpic_status lpic_load_plasma(lpic_ctx *c, const lpic_plasma_params *p) {
     return LPIC_OK;
 }
 
+// Record one step (with_sort: followed by the counting sort) as a CUDA graph.  The particle
+// kernels are sized for the whole capacity (they read the live count from the device), so the
+// graph stays valid while the particle count changes.
+lpic_status capture_step(lpic_ctx *c, int with_sort) {
+    static_assert(lpic_ctx::kFamilies == 9, "step_launches is sized for the kernel families");
+    long long before[lpic_ctx::kFamilies];
+    memcpy(before, c->launches, sizeof before);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return c->cuda_fail(e, "step capture");
+    const int npl = (int)c->g.particle_capacity, inj = inj_upper(c);
+    c->dispatch([&](auto &S) {
+        enqueue_step_kernels(c, S, npl, inj, c->st);
+        if (with_sort)
+            traced(c, F_SORT, kSortLaunches, c->st, [&] { launch_sort(S, npl, c->key, c->count, c->blocksum, c->st); });
+    });
+    e = cudaStreamEndCapture(c->st, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec[with_sort], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int f = 0; f < lpic_ctx::kFamilies; f++) {
+        c->step_launches[with_sort][f] = c->launches[f] - before[f];
+        c->launches[f] = before[f];
+    }
+    return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "step graph");
+}
+
 lpic_status lpic_step(lpic_ctx *c, int nsteps) {
     if (!c) return LPIC_EINVAL;
     if (nsteps < 0) return c->fail(LPIC_EINVAL, "nsteps < 0");
@@ -584,9 +619,17 @@ lpic_status lpic_step(lpic_ctx *c, int nsteps) {
     if (s != LPIC_OK) return s;
     for (int k = 0; k < nsteps; k++) {
         pre_step(c, c->st);
-        const int npl = launch_cap(c), inj = inj_upper(c);
-        c->dispatch([&](auto &S) { enqueue_step_kernels(c, S, npl, inj, c->st); });
-        post_step(c, c->st);
+        if (c->timing) {   // kernel by kernel, bracketed with events
+            const int npl = launch_cap(c), inj = inj_upper(c);
+            c->dispatch([&](auto &S) { enqueue_step_kernels(c, S, npl, inj, c->st); });
+            post_step(c, c->st);
+            continue;
+        }
+        const int sort = advance_mirror(c) ? 1 : 0;   // host mirrors of this step; sort after it?
+        if (!c->step_exec[sort] && (s = capture_step(c, sort)) != LPIC_OK) return s;
+        cudaError_t e = cudaGraphLaunch(c->step_exec[sort], c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "lpic_step");
+        for (int f = 0; f < lpic_ctx::kFamilies; f++) c->launches[f] += c->step_launches[sort][f];
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return c->cuda_fail(e, "lpic_step");
@@ -941,6 +984,7 @@ const char *lpic_kernel_name(int k) {
 lpic_status lpic_destroy(lpic_ctx *c) {
     if (!c) return LPIC_EINVAL;
     cudaStreamSynchronize(c->st);
+    c->drop_step_graphs();
     for (auto &sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->ev) cudaEventDestroy(c->ev);
