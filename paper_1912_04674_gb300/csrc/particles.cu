@@ -101,19 +101,13 @@ template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r,
     }
 }
 
-// q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 254), assembled from the
-// IEEE-754 fields with 32-bit integer operations (the FP64 pipe is slow on this part): |q| is
-// normalised so that its leading one sits at bit 31, the 31 bits below it become the top of
-// the 52-bit fraction, and the exponent is the position of that one plus e - 151.
+// q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 254): the integer converts
+// to FP64 exactly (one conversion per value, issued by the run heads only), and the power of
+// two is added to its exponent field, which stays in the normal range for these q and e.
+// (Measured faster than assembling the bits with 32-bit integer operations.)
 __device__ __forceinline__ double scaled_int_to_double(int q, int e) {
-    const unsigned sgn = (unsigned)q & 0x80000000u;
-    const unsigned a = q < 0 ? 0u - (unsigned)q : (unsigned)q;
-    const int lz = __clz(a);
-    const unsigned n = a << lz;                                        // leading one at bit 31
-    const unsigned ex = (unsigned)(1023 + (31 - lz) + (e - 151));
-    const unsigned hi = sgn | (ex << 20) | ((n >> 11) & 0xfffffu);
-    const unsigned lo = n << 21;
-    return __hiloint2double((int)hi, (int)lo);
+    const double d = (double)q;
+    return __hiloint2double(__double2hiint(d) + ((e - 151) << 20), __double2loint(d));
 }
 
 // Deposit of each run's four values (row factors already applied; the lanes of a run share
