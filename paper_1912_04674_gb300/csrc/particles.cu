@@ -88,10 +88,13 @@ __device__ __forceinline__ Run run_of(unsigned key) {
 }
 
 // Segmented suffix sums: afterwards the head lane of each run holds the run's sums.
+// Stages stop at the warp's longest run (sorted particles rarely make runs of 32 lanes).
 template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r, T (&v)[N]) {
     const int lane = threadIdx.x & 31;
+    const int span = (int)__reduce_max_sync(FULL, (unsigned)(r.end - r.head));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+        if (o >= span) break;
         const bool in = lane + o < r.end;
 #pragma unroll
         for (int q = 0; q < N; q++) {
