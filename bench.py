@@ -350,51 +350,77 @@ def served_scan(n_jobs: int, rate: float = 2.0, budget_gb: float = 150.0):
     return rep
 
 
-def batched_scan(n_sims: int, steps: int, warmup: int = 5):
+SMALL_SCAN = {"nx_range": (128, 384), "nr_range": (32, 64)}
+
+
+def batched_scan(n_sims: int, steps: int, warmup: int = 5, rounds: int = 4, nx_range=(256, 2048),
+                 nr_range=(64, 256)):
     """Batched parametric scan (FP32_MIXED): n_sims uneven simulations drawn like the scan
-    workload, advanced together by one fused launch per phase per step.  Beside it, the same
-    simulations stepped by their own single-simulation launches on their own streams."""
+    workload, advanced together as one batch with the schedule its autotuner picks (fused
+    launches, one per phase per step, or the simulations' own step graphs).  Beside it, the
+    same simulations stepped one call each from Python on their own streams.  The two forms
+    alternate in chunks of steps/rounds on the same (slowly growing) states, and each chunk's
+    throughput counts the particles alive when it starts, so both see the same work."""
     import torch
 
     from paper_1912_04674_gb300 import autotune, serve
     from paper_1912_04674_gb300 import lpic as L
     import workloads
-    jobs = workloads.scan_jobs(n_sims)
+    jobs = workloads.scan_jobs(n_sims, nx_range=nx_range, nr_range=nr_range)
     sims = [serve.make_simulation(w, "fp32", autotune.sort_every_for(w.nx, w.nr, w.ppc, "fp32"))
             for w in jobs]
     torch.cuda.synchronize()
     b = L.Batch(sims)
     tile, packs = autotune.tune_batch(b, "fp32")   # real steps of the batch, untimed
     b.step([warmup] * n_sims)
-    alive = sum(s.counters()["alive"] for s in sims)
-    l0 = b.launches()
+    for s in sims:                                 # warm the single-simulation graphs too
+        s.step(1)
+    chunk = max(1, steps // rounds)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    torch.cuda.synchronize()
-    ev[0].record(b.stream)
-    b.step([steps] * n_sims)
-    ev[1].record(b.stream)
-    torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1]) / steps
-    launches = b.launches() - l0
+    bat = {"ms": 0.0, "ps": 0.0, "steps": 0}
+    own = {"ms": 0.0, "ps": 0.0, "steps": 0}
+    launches = 0
+    for _ in range(rounds):
+        alive = sum(s.counters()["alive"] for s in sims)
+        l0 = b.launches()
+        torch.cuda.synchronize()
+        ev[0].record(b.stream)
+        b.step([chunk] * n_sims)
+        ev[1].record(b.stream)
+        torch.cuda.synchronize()
+        bat["ms"] += ev[0].elapsed_time(ev[1])
+        bat["ps"] += alive * chunk
+        bat["steps"] += chunk
+        launches += b.launches() - l0
+        # each simulation stepped by its own call, on its own stream, all streams in flight
+        # (host clock: the launches of 64 streams are part of what this form costs)
+        alive = sum(s.counters()["alive"] for s in sims)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(chunk):
+            for s in sims:
+                s.step(1)
+        torch.cuda.synchronize()
+        own["ms"] += (time.perf_counter() - t0) * 1e3
+        own["ps"] += alive * chunk
+        own["steps"] += chunk
     b.close()
-    # unfused: each simulation's own launches on its own stream, all streams in flight
-    k2 = max(3, steps // 4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(k2):
-        for s in sims:
-            s.step(1)
-    torch.cuda.synchronize()
-    ms_streams = (time.perf_counter() - t0) * 1e3 / k2
     for s in sims:
         s.close()
     torch.cuda.empty_cache()
-    return {"sims": n_sims, "steps": steps, "particles": alive, "ms_per_step": ms,
-            "value": alive / (ms * 1e-3), "unit": "particle-steps/s",
-            "gpu_launches_per_step": launches / steps, "particles_per_item": tile, "packs": packs,
+    ms = bat["ms"] / bat["steps"]
+    return {"sims": n_sims, "steps": bat["steps"], "particles": alive, "ms_per_step": ms,
+            "value": bat["ps"] / (bat["ms"] * 1e-3), "unit": "particle-steps/s",
+            "gpu_launches_per_step": launches / bat["steps"], "particles_per_item": tile,
+            "packs": packs,
             "tuning_ms_per_step": [[c, p, round(m, 3)] for c, p, m in getattr(b, "tuning_log", [])],
-            "per_sim_streams_ms_per_step": ms_streams,
-            "workload": "64 scan sims: Nx~U{256..2048}, Nr~U{64..256}, a0~U[0.5,3], "
+            "per_sim_streams": {"ms_per_step": own["ms"] / own["steps"],
+                                "value": own["ps"] / (own["ms"] * 1e-3), "steps": own["steps"]},
+            "batch_over_streams": (bat["ps"] / bat["ms"]) / (own["ps"] / own["ms"]),
+            "schedule": "unfused (own step graphs)" if packs < 0 else "fused",
+            "interleaved_rounds": rounds,
+            "workload": f"{n_sims} scan sims: Nx~U{{{nx_range[0]}..{nx_range[1]}}}, "
+                        f"Nr~U{{{nr_range[0]}..{nr_range[1]}}}, a0~U[0.5,3], "
                         "n0 log-U[5e-4,5e-3], w0~U[30,80], 2x2x4 ppc, FP32_MIXED, early steps"}
 
 
@@ -568,7 +594,10 @@ def run_ours(args):
     acc = accuracy(args.settle + args.warmup + result["fp64"]["steps"]) if extras else None
     e2e = e2e_run("fp32", args.steps, args.settle) if extras else None
     cpu = cpu_baseline() if (extras and world == 1 and not args.no_cpu) else None
-    batch = batched_scan(args.batch_sims, args.batch_steps) if (extras and args.batch_sims > 0) else None
+    batch = None
+    if extras and args.batch_sims > 0:
+        batch = batched_scan(args.batch_sims, args.batch_steps)
+        batch["small_sims"] = batched_scan(args.batch_sims, args.batch_steps, **SMALL_SCAN)
     large = large_run() if (extras and not args.no_large) else None
     filt = filter_leg() if extras else None
     bunch = bunch_leg() if extras else None
@@ -673,7 +702,9 @@ def main():
     from paper_1912_04674_gb300 import build
     build.build()
     if args.only == "batch":
-        print(json.dumps({"profile_run": True, "batch": batched_scan(args.batch_sims, args.batch_steps)}))
+        batch = batched_scan(args.batch_sims, args.batch_steps)
+        batch["small_sims"] = batched_scan(args.batch_sims, args.batch_steps, **SMALL_SCAN)
+        print(json.dumps({"profile_run": True, "batch": batch}))
         return
     if args.only == "large":
         print(json.dumps({"profile_run": True, "large_run": large_run()}))

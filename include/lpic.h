@@ -265,7 +265,9 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
  *   better, larger ones cost less per item.
  * packs: split the simulations into this many packs (0: as few as the parameter space
  *   allows, one per 48 simulations), each with its own launch sequence as a parallel branch
- *   of the graph, so that phases of different packs overlap on the device.
+ *   of the graph, so that phases of different packs overlap on the device.  -1: no fused
+ *   launches; each step replays every simulation's own step graph (lpic_step) on its own
+ *   stream, in turn, which overlaps better for batches of large simulations.
  * The binding's autotuner picks both by timing real steps.  Errors: LPIC_EINVAL. */
 lpic_status lpic_batch_set_tuning(lpic_batch *b, int32_t particles_per_item, int32_t packs);
 /* Kernels the batch has enqueued so far (fused launches, relocations and sorts). */

@@ -10,8 +10,9 @@ parameter scan reuses a handful of measurements.
 The fused particle passes of a batch walk items of a fixed number of particle slots; small
 items balance the blocks, large ones cost less per item.  The batch tuner times real steps
 of the batch itself (the simulations advance while it measures, so no work is wasted) for
-each candidate item size and pack count and keeps the fastest, cached per precision, sim
-count and total-capacity bucket.
+each candidate item size and pack count, and the unfused schedule (each simulation's own
+step graph on its own stream, which overlaps better when the simulations are large), and
+keeps the fastest, cached per precision, sim count and total-capacity bucket.
 """
 from __future__ import annotations
 
@@ -115,10 +116,11 @@ def _time_batch(batch, steps: int) -> float:
 def tune_batch(batch, precision: str, steps: int = 4, tiles=TILE_CANDIDATES,
                packs=PACK_CANDIDATES) -> tuple[int, int]:
     """Pick the work-item size and the pack count of `batch` (an lpic.Batch) by timing
-    `steps` real batch steps per candidate (item size first, then packs at the best size);
-    sets the winner on the batch, caches it and returns (particles_per_item, packs); the
-    measurements are left in batch.tuning_log.  Every simulation of the batch advances
-    (1 + steps) steps per candidate."""
+    `steps` real batch steps per candidate (item size first, then packs at the best size,
+    then packs = -1: the simulations' own step graphs, unfused); sets the winner on the
+    batch, caches it and returns (particles_per_item, packs); the measurements are left in
+    batch.tuning_log.  Every simulation of the batch advances (1 + steps) steps per
+    candidate."""
     total = sum(int(s.gs.particle_capacity) for s in batch.sims)
     key = _batch_bucket(total, len(batch.sims), precision)
     with _lock:
@@ -134,8 +136,8 @@ def tune_batch(batch, precision: str, steps: int = 4, tiles=TILE_CANDIDATES,
         batch.tuning_log.append((c, 0, ms))
         if ms < best_ms:
             best, best_ms = (c, 0), ms
-    for p in packs:
-        if p <= 0 or p > len(batch.sims):
+    for p in tuple(packs) + (-1,):
+        if p == 0 or p > len(batch.sims):
             continue
         batch.set_tuning(best[0], p)
         ms = _time_batch(batch, steps)

@@ -1026,7 +1026,10 @@ int window_work(const lpic_ctx *c) {
 }
 
 int pack_count(int n) { return (n + kPackMax - 1) / kPackMax; }
-size_t flags_bytes(int n) { return ((size_t)n * sizeof(int) + 255) / 256 * 256; }
+// Head of the batch buffer: n sort flags, then three item tickets per pack (pass A, pass B,
+// pass B with the charge change; at most n packs).
+constexpr int kTicketsPerPack = 3;
+size_t flags_bytes(int n) { return ((size_t)n * (1 + kTicketsPerPack) * sizeof(int) + 255) / 256 * 256; }
 
 // Upper bound of the work items over all lists with every simulation active.
 size_t batch_items_bound(lpic_ctx *const *ctxs, int n) {
@@ -1054,7 +1057,8 @@ struct lpic_batch {
     std::vector<lpic_ctx *> ctx;
     lpic_precision prec = LPIC_FP64;
     cudaStream_t st = nullptr;
-    int *due = nullptr;                     // caller's device buffer: sort flags, then items
+    int *due = nullptr;                     // caller's device buffer: sort flags, tickets, items
+    int *tickets = nullptr;
     int4 *items = nullptr;
     size_t items_cap = 0;
     cudaEvent_t ev = nullptr;
@@ -1130,6 +1134,29 @@ void plan_pack(const lpic_batch *b, const std::vector<int> &sims, std::vector<in
         }
 }
 
+// Grid, window and sort kernels of the batch graph run at the device's greatest priority: when
+// one pack's particle pass ends, its next grid phase is dispatched ahead of the blocks still
+// waiting in other packs' particle passes, so the packs' chains keep overlapping.
+template <class R> void prioritise_grid_nodes(cudaGraph_t graph) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess || least == greatest) return;
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn == 0) return;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return;
+    for (size_t q = 0; q < nn; q++) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[q], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nodes[q], &kp) != cudaSuccess) continue;
+        if (is_particle_multi_kernel<R>(kp.func)) continue;
+        cudaKernelNodeAttrValue v = {};
+        v.priority = greatest;
+        cudaGraphKernelNodeSetAttribute(nodes[q], cudaKernelNodeAttributePriority, &v);
+    }
+    cudaGetLastError();   // a refused attribute leaves the default priority
+}
+
 // Upload the work lists, then record one step of the active set, without and with the
 // sorts (the sort launches act on the simulations whose flag is set before the replay).
 template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
@@ -1179,6 +1206,7 @@ template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<ch
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        cudaMemsetAsync(b->tickets, 0, (size_t)npk * kTicketsPerPack * sizeof(int), b->st);
         cudaEventRecord(b->ev, b->st);
         int nl = 0;
         for (int p = 0; p < npk; p++) {
@@ -1190,10 +1218,11 @@ template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<ch
             for (int q : {BL_PREPASS, BL_SLOTS, BL_ENVELOPE, BL_PASSB, BL_PASSB_DQ, BL_FILTER, BL_AMPERE, BL_WINDOW})
                 nl += cn[q] > 0;
             launch_grid_multi<R>(0, *pk, it(BL_PREPASS), cn[BL_PREPASS], st);
-            launch_particles_multi<R>(0, false, *pk, it(BL_SLOTS), cn[BL_SLOTS], st);
+            int *tk = b->tickets + (size_t)p * kTicketsPerPack;
+            launch_particles_multi<R>(0, false, *pk, it(BL_SLOTS), cn[BL_SLOTS], tk, st);
             launch_grid_multi<R>(1, *pk, it(BL_ENVELOPE), cn[BL_ENVELOPE], st);
-            launch_particles_multi<R>(1, false, *pk, it(BL_PASSB), cn[BL_PASSB], st);
-            launch_particles_multi<R>(1, true, *pk, it(BL_PASSB_DQ), cn[BL_PASSB_DQ], st);
+            launch_particles_multi<R>(1, false, *pk, it(BL_PASSB), cn[BL_PASSB], tk + 1, st);
+            launch_particles_multi<R>(1, true, *pk, it(BL_PASSB_DQ), cn[BL_PASSB_DQ], tk + 2, st);
             launch_grid_multi<R>(3, *pk, it(BL_FILTER), cn[BL_FILTER], st);
             launch_grid_multi<R>(2, *pk, it(BL_AMPERE), cn[BL_AMPERE], st);
             launch_window_multi<R>(*pk, it(BL_WINDOW), cn[BL_WINDOW], st);
@@ -1208,7 +1237,10 @@ template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<ch
             }
         }
         e = cudaStreamEndCapture(b->st, &graph);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[g], graph, 0);
+        if (e == cudaSuccess) {
+            prioritise_grid_nodes<R>(graph);
+            e = cudaGraphInstantiate(&b->exec[g], graph, cudaGraphInstantiateFlagUseNodePriority);
+        }
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
         b->per_replay[g] = nl;
@@ -1249,6 +1281,7 @@ lpic_status lpic_batch_create(lpic_batch **out, lpic_ctx *const *ctxs, int n, vo
     b->prec = ctxs[0]->prec;
     b->st = (cudaStream_t)cuda_stream;
     b->due = (int *)device_buf;
+    b->tickets = b->due + n;
     b->items = (int4 *)((char *)device_buf + flags_bytes(n));
     b->items_cap = (buf_bytes - flags_bytes(n)) / sizeof(int4);
     cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
@@ -1271,6 +1304,33 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps) {
         if (steps[k] > maxs) maxs = steps[k];
     }
     if (maxs == 0) return LPIC_OK;
+    if (b->packs < 0) {
+        // each simulation's own step graph on its own stream, in turn, after earlier work on
+        // the batch stream; later work on the batch stream comes after all of them
+        cudaEventRecord(b->ev, b->st);
+        for (size_t k = 0; k < n; k++) cudaStreamWaitEvent(b->ctx[k]->st, b->ev, 0);
+        for (int t = 0; t < maxs; t++)
+            for (size_t k = 0; k < n; k++) {
+                if (steps[k] <= t) continue;
+                lpic_ctx *c = b->ctx[k];
+                long long before = 0, after = 0;
+                for (int f = 0; f < lpic_ctx::kFamilies; f++) before += c->launches[f];
+                const lpic_status s = lpic_step(c, 1);
+                if (s != LPIC_OK) {
+                    b->err = "batch: simulation " + std::to_string(k) + ": " + c->err;
+                    return s;
+                }
+                for (int f = 0; f < lpic_ctx::kFamilies; f++) after += c->launches[f];
+                b->launches += after - before;
+            }
+        for (size_t k = 0; k < n; k++) {
+            cudaEventRecord(b->ev, b->ctx[k]->st);
+            cudaStreamWaitEvent(b->st, b->ev, 0);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
+        return LPIC_OK;
+    }
     // order after earlier work on the contexts' own streams
     for (size_t k = 0; k < n; k++) {
         cudaEventRecord(b->ev, b->ctx[k]->st);
@@ -1321,7 +1381,7 @@ lpic_status lpic_batch_set_tuning(lpic_batch *b, int32_t particles_per_item, int
         b->err = "batch: particles_per_item must be a multiple of 256 in [1024, 1048576]";
         return LPIC_EINVAL;
     }
-    if (packs < 0) { b->err = "batch: packs must be >= 0"; return LPIC_EINVAL; }
+    if (packs < -1) { b->err = "batch: packs must be >= -1"; return LPIC_EINVAL; }
     if (particles_per_item != b->chunk || packs != b->packs) {
         b->chunk = particles_per_item;
         b->packs = packs;

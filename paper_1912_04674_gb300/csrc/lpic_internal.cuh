@@ -313,10 +313,13 @@ void grid_tiles(const Geo &g, int phase, int &tx, int &ty);
 template <class R>
 void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);
 // particle phases (0 pass A, 1 pass B): items {sim, item, 0, slots per item}, item covering
-// slots [item * size, (item + 1) * size) clipped to the live slots
+// slots [item * size, (item + 1) * size) clipped to the live slots; blocks draw the items
+// from *ticket, which must be zero when the launch starts
 template <class R>
 void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4 *items, int n,
-                            cudaStream_t st);
+                            int *ticket, cudaStream_t st);
+// whether f is the entry point of one of the fused particle kernels above
+template <class R> bool is_particle_multi_kernel(const void *f);
 // window: items {sim, part, parts of sim, 0}
 template <class R> void launch_window_multi(const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);
 // counting sort of the simulations with due[slot] != 0, seven launches: clear, count, scan

@@ -465,18 +465,26 @@ __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b(SimDev<R
     pass_b_body<R, DQ>(S, blockIdx.x, gridDim.x, 0);
 }
 
-// Fused forms over a batch: each block walks work items {simulation, item, 0, slots per
-// item}.
+// Fused forms over a batch: blocks take work items {simulation, item, 0, slots per item} in
+// turn from a ticket counter (zeroed before the launch), so that the blocks that drew cheap
+// items take more of them and the launch ends with little tail.
+__device__ __forceinline__ int next_item(int *ticket) {
+    __shared__ int w;
+    __syncthreads();   // every thread has read the previous ticket
+    if (threadIdx.x == 0) w = atomicAdd(ticket, 1);
+    __syncthreads();
+    return w;
+}
 template <class R>
-__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n, int *ticket) {
+    for (int w = next_item(ticket); w < n; w = next_item(ticket)) {
         const int4 it = items[w];
         pass_a_body<R>(pk.v[it.x], it.y, it.z, it.w);
     }
 }
 template <class R, bool DQ>
-__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
-    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_b_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n, int *ticket) {
+    for (int w = next_item(ticket); w < n; w = next_item(ticket)) {
         const int4 it = items[w];
         pass_b_body<R, DQ>(pk.v[it.x], it.y, it.z, it.w);
     }
@@ -545,24 +553,30 @@ template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_col
 
 template <class R>
 void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4 *items, int n,
-                            cudaStream_t st) {
+                            int *ticket, cudaStream_t st) {
     if (n <= 0) return;
     int g;
     if (phase == 0) {
         g = resident_blocks(k_pass_a_multi<R>);
-        k_pass_a_multi<R><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
+        k_pass_a_multi<R><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n, ticket);
     } else if (dq) {
         g = resident_blocks(k_pass_b_multi<R, true>);
-        k_pass_b_multi<R, true><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
+        k_pass_b_multi<R, true><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n, ticket);
     } else {
         g = resident_blocks(k_pass_b_multi<R, false>);
-        k_pass_b_multi<R, false><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n);
+        k_pass_b_multi<R, false><<<n < g ? n : g, TPB, 0, st>>>(pk, items, n, ticket);
     }
 }
 
+template <class R> bool is_particle_multi_kernel(const void *f) {
+    return f == (const void *)k_pass_a_multi<R> || f == (const void *)k_pass_b_multi<R, false> ||
+           f == (const void *)k_pass_b_multi<R, true>;
+}
+
 #define INST(R)                                                                             \
+    template bool is_particle_multi_kernel<R>(const void *);                                \
     template void launch_particles_multi<R>(int, bool, const SimPack<R> &, const int4 *, int, \
-                                            cudaStream_t);                                  \
+                                            int *, cudaStream_t);                           \
     template void launch_pass_a<R>(const SimDev<R> &, int, cudaStream_t);                   \
     template void launch_pass_b<R>(const SimDev<R> &, int, cudaStream_t);                   \
     template void launch_load_columns<R>(const SimDev<R> &, const int *, int, int, cudaStream_t);

@@ -56,6 +56,59 @@ def test_batch_matches_alone(precision, tol):
         assert a.counters() == m.counters()
 
 
+def test_unfused_schedule_matches_alone():
+    """packs = -1: every batch step replays each simulation's own step graph, in turn."""
+    import torch
+
+    from paper_1912_04674_gb300 import lpic as L
+    jobs = small_jobs()
+    steps = [30, 45, 20]
+    alone = []
+    for w, n in zip(jobs, steps):
+        s = gpu_from(w, precision="fp32")
+        s.step(n)
+        alone.append(s)
+    mixed = [gpu_from(w, precision="fp32") for w in jobs]
+    b = L.Batch(mixed, torch.cuda.Stream())
+    b.set_tuning(4096, -1)
+    b.step(steps)
+    assert b.launches() > 0
+    b.close()
+    for a, m, n in zip(alone, mixed, steps):
+        assert m.counters()["step"] == n
+        for f in ("ex", "er", "bt", "a", "chi", "jx"):
+            assert rel_err(m.field(f), a.field(f)) < 1e-5, (f, rel_err(m.field(f), a.field(f)))
+        assert a.counters() == m.counters()
+
+
+def test_batch_interleaved_with_own_steps_matches_alone():
+    """Batch steps and each simulation's own steps alternate on the same states (the host
+    mirrors and the device state are the simulation's; the batch holds none of its own)."""
+    import torch
+
+    from paper_1912_04674_gb300 import lpic as L
+    jobs = small_jobs()
+    alone = []
+    for w in jobs:
+        s = gpu_from(w, precision="fp32")
+        s.step(33)
+        alone.append(s)
+    mixed = [gpu_from(w, precision="fp32") for w in jobs]
+    b = L.Batch(mixed, torch.cuda.Stream())
+    b.step([6, 6, 6])
+    for s, n in zip(mixed, (7, 11, 3)):
+        s.step(n)
+    b.step([12, 8, 16])
+    for s, n in zip(mixed, (8, 8, 8)):
+        s.step(n)
+    b.close()
+    for a, m in zip(alone, mixed):
+        assert m.counters()["step"] == 33
+        for f in ("ex", "er", "bt", "a", "chi", "jx"):
+            assert rel_err(m.field(f), a.field(f)) < 1e-5, (f, rel_err(m.field(f), a.field(f)))
+        assert a.counters() == m.counters()
+
+
 def test_batch_larger_than_one_pack_matches_alone():
     """More simulations than one launch's parameter pack holds: the batch splits them into
     packs whose launch sequences run as parallel graph branches."""
