@@ -1134,29 +1134,6 @@ void plan_pack(const lpic_batch *b, const std::vector<int> &sims, std::vector<in
         }
 }
 
-// Grid, window and sort kernels of the batch graph run at the device's greatest priority: when
-// one pack's particle pass ends, its next grid phase is dispatched ahead of the blocks still
-// waiting in other packs' particle passes, so the packs' chains keep overlapping.
-template <class R> void prioritise_grid_nodes(cudaGraph_t graph) {
-    int least = 0, greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess || least == greatest) return;
-    size_t nn = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn == 0) return;
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return;
-    for (size_t q = 0; q < nn; q++) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nodes[q], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
-        cudaKernelNodeParams kp;
-        if (cudaGraphKernelNodeGetParams(nodes[q], &kp) != cudaSuccess) continue;
-        if (is_particle_multi_kernel<R>(kp.func)) continue;
-        cudaKernelNodeAttrValue v = {};
-        v.priority = greatest;
-        cudaGraphKernelNodeSetAttribute(nodes[q], cudaKernelNodeAttributePriority, &v);
-    }
-    cudaGetLastError();   // a refused attribute leaves the default priority
-}
-
 // Upload the work lists, then record one step of the active set, without and with the
 // sorts (the sort launches act on the simulations whose flag is set before the replay).
 template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<char> &active) {
@@ -1237,10 +1214,7 @@ template <class R> lpic_status batch_capture(lpic_batch *b, const std::vector<ch
             }
         }
         e = cudaStreamEndCapture(b->st, &graph);
-        if (e == cudaSuccess) {
-            prioritise_grid_nodes<R>(graph);
-            e = cudaGraphInstantiate(&b->exec[g], graph, cudaGraphInstantiateFlagUseNodePriority);
-        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[g], graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) { b->err = std::string("graph: ") + cudaGetErrorString(e); return LPIC_ECUDA; }
         b->per_replay[g] = nl;

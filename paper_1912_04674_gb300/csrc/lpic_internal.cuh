@@ -318,8 +318,6 @@ void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n
 template <class R>
 void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4 *items, int n,
                             int *ticket, cudaStream_t st);
-// whether f is the entry point of one of the fused particle kernels above
-template <class R> bool is_particle_multi_kernel(const void *f);
 // window: items {sim, part, parts of sim, 0}
 template <class R> void launch_window_multi(const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st);
 // counting sort of the simulations with due[slot] != 0, seven launches: clear, count, scan

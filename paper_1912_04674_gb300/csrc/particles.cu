@@ -568,13 +568,7 @@ void launch_particles_multi(int phase, bool dq, const SimPack<R> &pk, const int4
     }
 }
 
-template <class R> bool is_particle_multi_kernel(const void *f) {
-    return f == (const void *)k_pass_a_multi<R> || f == (const void *)k_pass_b_multi<R, false> ||
-           f == (const void *)k_pass_b_multi<R, true>;
-}
-
 #define INST(R)                                                                             \
-    template bool is_particle_multi_kernel<R>(const void *);                                \
     template void launch_particles_multi<R>(int, bool, const SimPack<R> &, const int4 *, int, \
                                             int *, cudaStream_t);                           \
     template void launch_pass_a<R>(const SimDev<R> &, int, cudaStream_t);                   \
