@@ -3,10 +3,11 @@
 // removal at the window edges) and the lattice loader.
 //
 // Each block walks particle slots in block-sized groups (a block-uniform loop: every lane
-// takes part in the warp reductions and the blocks may synchronise).  Particles are kept
-// counting-sorted by cell, so runs of neighbouring lanes deposit onto the same nodes: each
-// deposit is first summed over its run with a segmented shuffle reduction (exact, in
-// integers, in FP32), and only one lane per run and deposit issues the FP64 global atomic.
+// takes part in the warp reductions and the blocks may synchronise); the FP32 pass A takes two
+// neighbouring slots per thread.  Particles are kept counting-sorted by cell, so runs of
+// neighbouring lanes deposit onto the same nodes: each deposit is first summed over its run
+// with a segmented shuffle reduction (exact, in integers, in FP32), and only one lane per run
+// and deposit issues the FP64 global atomic.
 #include <mutex>
 
 #include "lpic_internal.cuh"
@@ -192,14 +193,82 @@ __device__ __forceinline__ int2 slot_range(int np, int vb, int nvb, int csize) {
     return make_int2(begin, min(begin + chunk, np));
 }
 
+// Results of pass A for one particle: its susceptibility deposit (four primal nodes from b,
+// row factors applied, with a bound on their size) and its new momentum.
+template <class R> struct AOut {
+    unsigned key;   // b, or kNoKey for a hole
+    int b;
+    R v[4], bnd;
+    R px, py, pz;
+};
+
+template <class R>
+__device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo, int off, long long shift,
+                                              int ix, R ox, R y, R z, R px, R py, R pz, R w) {
+    const R hdt = S.k.hdt, idr = S.k.idr;
+    const R *__restrict__ tchi = S.k.tab + T_CHI * geo.P;
+    const R q = (R)-1;
+    const bool alive = ix != kDead;
+    const int irel = (int)((long long)ix - shift);
+    const R r2 = y * y + z * z;
+    const bool onaxis = !(r2 > (R)0);
+    const R ir = onaxis ? (R)0 : rsqrt_<R>(r2);
+    const R r = r2 * ir, ct = onaxis ? (R)1 : y * ir, st = z * ir;
+    const Loc<R> L = locate<R>(irel, ox, r * idr, geo.nx, geo.nr);
+    const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
+    const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
+    const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
+    // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
+    const int b = geo.at(off, L.ip, L.jp);
+    const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
+    const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
+    const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
+    const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
+    const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
+    const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
+    const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
+    const R Ex = exg, Ey = erg * ct, Ez = erg * st;
+    const R By = -btg * st, Bz = btg * ct;               // Bx = 0
+    const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
+
+    const R i2g0 = (R)0.5 * rsqrt_<R>((R)1 + px * px + py * py + pz * pz + phg);
+    const R sx = px + hdt * (q * Ex - Gx * i2g0);
+    const R sy = py + hdt * (q * Ey - Gy * i2g0);
+    const R sz = pz + hdt * (q * Ez - Gz * i2g0);
+    const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
+
+    // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1), 1/V per row
+    AOut<R> o;
+    const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
+    const R base_w = alive ? w * rgt : (R)0;
+    const R c0 = base_w * i0, c1 = base_w * i1;
+    o.v[0] = c0 * w00; o.v[1] = c0 * w10; o.v[2] = c1 * w01; o.v[3] = c1 * w11;
+    o.bnd = c0 > c1 ? c0 : c1;
+    o.key = alive ? (unsigned)b : kNoKey;
+    o.b = b;
+
+    const R i2gt = (R)0.5 * rgt;
+    const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
+    const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
+    const R tf = q * hdt * rsqrt_<R>((R)1 + mx * mx + my * my + mz * mz + phg);
+    const R ty = tf * By, tz = tf * Bz;                  // tx = 0
+    const R sf = (R)2 / ((R)1 + ty * ty + tz * tz);
+    const R vy = sf * ty, vz = sf * tz;
+    // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
+    const R ppx = mx + (my * tz - mz * ty);
+    const R ppy = my + (-mx * tz);
+    const R ppz = mz + (mx * ty);
+    o.px = mx + (ppy * vz - ppz * vy) + hdt * Fx;
+    o.py = my + (-ppx * vz) + hdt * Fy;
+    o.pz = mz + (ppx * vy) + hdt * Fz;
+    return o;
+}
+
 template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &S, int vb, int nvb, int csize) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
     const long long shift = S.d->shift;
-    const R hdt = S.k.hdt, idr = S.k.idr;
-    const R *__restrict__ tchi = S.k.tab + T_CHI * geo.P;
-    const R q = (R)-1;
     // each block walks one contiguous chunk of slots, so that its successive iterations
     // gather from neighbouring cells (field lines stay in L1)
     const int2 rg = slot_range(np, vb, nvb, csize);
@@ -208,69 +277,168 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
     PReg<R> cur = load_particle<R>(P, k, end);
     for (int base = begin; base < end; base += TPB, k += TPB) {
         const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
-        const bool alive = cur.ix != kDead;
-        const int irel = (int)((long long)cur.ix - shift);
-        const R y = cur.y, z = cur.z, w = cur.w, px = cur.px, py = cur.py, pz = cur.pz;
-        const R r2 = y * y + z * z;
-        const bool onaxis = !(r2 > (R)0);
-        const R ir = onaxis ? (R)0 : rsqrt_<R>(r2);
-        const R r = r2 * ir, ct = onaxis ? (R)1 : y * ir, st = z * ir;
-        const Loc<R> L = locate<R>(irel, cur.ox, r * idr, geo.nx, geo.nr);
-        const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
-        const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
-        const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
-        // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
-        const int b = geo.at(off, L.ip, L.jp);
-        const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
-        const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
-        const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
-        const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
-        const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
-        const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
-        const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
-        const R Ex = exg, Ey = erg * ct, Ez = erg * st;
-        const R By = -btg * st, Bz = btg * ct;               // Bx = 0
-        const R Gx = gxg, Gy = grg * ct, Gz = grg * st;
-
-        const R i2g0 = (R)0.5 * rsqrt_<R>((R)1 + px * px + py * py + pz * pz + phg);
-        const R sx = px + hdt * (q * Ex - Gx * i2g0);
-        const R sy = py + hdt * (q * Ey - Gy * i2g0);
-        const R sz = pz + hdt * (q * Ez - Gz * i2g0);
-        const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
-
-        // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1), 1/V per row
-        const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
-        const R base_w = alive ? w * rgt : (R)0;
-        const R c0 = base_w * i0, c1 = base_w * i1;
-        const R v[4] = {c0 * w00, c0 * w10, c1 * w01, c1 * w11};
-        const R bnd[1] = {c0 > c1 ? c0 : c1};
-        const unsigned key = alive ? (unsigned)b : kNoKey;
-
-        const R i2gt = (R)0.5 * rgt;
-        const R Fx = q * Ex - Gx * i2gt, Fy = q * Ey - Gy * i2gt, Fz = q * Ez - Gz * i2gt;
-        const R mx = px + hdt * Fx, my = py + hdt * Fy, mz = pz + hdt * Fz;
-        const R tf = q * hdt * rsqrt_<R>((R)1 + mx * mx + my * my + mz * mz + phg);
-        const R ty = tf * By, tz = tf * Bz;                  // tx = 0
-        const R sf = (R)2 / ((R)1 + ty * ty + tz * tz);
-        const R vy = sf * ty, vz = sf * tz;
-        // p' = p- + p- x t ; p+ = p- + p' x s   (t and s have no x component)
-        const R ppx = mx + (my * tz - mz * ty);
-        const R ppy = my + (-mx * tz);
-        const R ppz = mz + (mx * ty);
-        if (alive) {
-            P.px[k] = mx + (ppy * vz - ppz * vy) + hdt * Fx;
-            P.py[k] = my + (-ppx * vz) + hdt * Fy;
-            P.pz[k] = mz + (ppx * vy) + hdt * Fz;
+        const AOut<R> o = a_particle<R>(S, geo, off, shift, cur.ix, cur.ox, cur.y, cur.z, cur.px, cur.py,
+                                        cur.pz, cur.w);
+        if (cur.ix != kDead) {
+            P.px[k] = o.px;
+            P.py[k] = o.py;
+            P.pz[k] = o.pz;
         }
-        const Run run = run_of(key);
-        double *const addr[4] = {S.f.chi + b, S.f.chi + b + geo.P, S.f.chi + b + 1,
-                                 S.f.chi + b + geo.P + 1};
-        run_deposit<1>(run, key, v, bnd, addr);
+        const Run run = run_of(o.key);
+        const R bnd[1] = {o.bnd};
+        double *const addr[4] = {S.f.chi + o.b, S.f.chi + o.b + geo.P, S.f.chi + o.b + 1,
+                                 S.f.chi + o.b + geo.P + 1};
+        run_deposit<1>(run, o.key, o.v, bnd, addr);
         cur = nxt;
     }
 }
 
-template <class R> __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a(SimDev<R> S) {
+// ---- FP32: two neighbouring particles per thread ----------------------------------------------
+// Thread t of a block takes slots 2t and 2t+1 of each group of 2*TPB (8-byte vector loads and
+// stores), and the warp deposits its 64 particles as one sequence: element a then element b of
+// lane 0, then of lane 1, ...  Within a lane, b absorbs a when their cells agree.  A chain is a
+// run of lanes whose single (absorbed) element continues the previous lane's b cell; chains are
+// summed by a segmented prefix scan, so the chain's last lane holds its sum.  A lane whose a
+// and b differ deposits a itself, adding the sum of the chain that ends on the previous lane
+// when that chain has a's cell; a chain's last lane deposits b's sum unless the next lane's
+// first element continues it.  Values are scaled by 2^(150 - e) (64 values per warp) and the
+// sums are exact in 32-bit integers.  (Measured 12 % faster than one particle per thread:
+// fewer load, reduction and atomic instructions per particle.)
+
+// The position half of a pair (carried one iteration ahead) and the rest (loaded at the top
+// of the iteration that uses it).
+struct PPos {
+    int2 ix;
+    float2 ox, y, z;
+};
+struct PMom {
+    float2 px, py, pz, w;
+};
+__device__ __forceinline__ float2 ld_pair(const float *a, int k, bool two, bool one) {
+    if (two) return *reinterpret_cast<const float2 *>(a + k);
+    return make_float2(one ? a[k] : 0.f, 0.f);
+}
+__device__ __forceinline__ PPos load_pos(const Parts<float> &P, int k, int lim) {
+    const bool two = k + 1 < lim, one = k < lim;
+    PPos q;
+    if (two) q.ix = *reinterpret_cast<const int2 *>(P.ix + k);
+    else q.ix = make_int2(one ? P.ix[k] : kDead, kDead);
+    q.ox = ld_pair(P.ox, k, two, one);
+    q.y = ld_pair(P.y, k, two, one);
+    q.z = ld_pair(P.z, k, two, one);
+    return q;
+}
+__device__ __forceinline__ PMom load_mom(const Parts<float> &P, int k, int lim) {
+    const bool two = k + 1 < lim, one = k < lim;
+    PMom q;
+    q.px = ld_pair(P.px, k, two, one);
+    q.py = ld_pair(P.py, k, two, one);
+    q.pz = ld_pair(P.pz, k, two, one);
+    q.w = ld_pair(P.w, k, two, one);
+    return q;
+}
+
+// Deposit of a warp's 64 elements (see above); v*[q] belong to group q*M/4 with bounds
+// bnd[m] >= |value| over both elements.
+// Node q of an element with cell base b is acc[b + o[q]], o = {0, P, 1, P + 1} (chi) or
+// {0, 1, P0, P0 + P} with the caller's offsets.
+template <int M>
+__device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const float (&va)[4], const float (&vb)[4],
+                                             const float (&bnd)[M], double *acc_a, double *acc_b,
+                                             const int (&o)[4]) {
+    const int lane = threadIdx.x & 31;
+    int qa[4], qb[4], ec[M];
+    bool bad[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        const unsigned e = ((unsigned)__float_as_uint(bnd[m]) >> 23) & 0xffu;
+        const int emax = (int)__reduce_max_sync(FULL, e);
+        bad[m] = emax == 255;
+        ec[m] = min(max(emax, 25), 254);
+        const float sc = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
+#pragma unroll
+        for (int q = m * 4 / M; q < (m + 1) * 4 / M; q++) {
+            qa[q] = bad[m] ? 0 : __float2int_rn(va[q] * sc);
+            qb[q] = bad[m] ? 0 : __float2int_rn(vb[q] * sc);
+        }
+    }
+    const bool fold = ka == kb;              // a joins b (also when both are holes)
+#pragma unroll
+    for (int q = 0; q < 4; q++) qb[q] += fold ? qa[q] : 0;
+    const unsigned kprev = __shfl_up_sync(FULL, kb, 1);
+    const bool has_prev = lane > 0;
+    const bool cont = has_prev && fold && kb == kprev;              // b continues the previous chain
+    const bool a_joins = has_prev && !fold && ka == kprev;          // a closes the previous chain
+    const unsigned absorb = __ballot_sync(FULL, cont || a_joins);
+    const unsigned starts = __ballot_sync(FULL, !cont);
+    const unsigned le = 0xffffffffu >> (31u - (unsigned)lane);
+    const int head = 31 - __clz(starts & le);                      // first lane of this chain
+    const int span = (int)__reduce_max_sync(FULL, (unsigned)(lane - head + 1));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (o >= span) break;
+        const bool in = lane - o >= head;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int t = __shfl_up_sync(FULL, qb[q], o);
+            if (in) qb[q] += t;
+        }
+    }
+    // the previous lane's chain sum, for an a that closes it
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int t = __shfl_up_sync(FULL, qb[q], 1);
+        if (a_joins) qa[q] += t;
+    }
+    const bool dep_a = !fold && ka != kNoKey;
+    const bool dep_b = kb != kNoKey && (lane == 31 || !((absorb >> (lane + 1)) & 1u));
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int m = q * M / 4;
+        if (dep_a) {
+            if (bad[m]) atomicAdd(acc_a + o[q], __longlong_as_double(0x7ff8000000000000ll));
+            else if (qa[q] != 0) atomicAdd(acc_a + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
+        }
+        if (dep_b) {
+            if (bad[m]) atomicAdd(acc_b + o[q], __longlong_as_double(0x7ff8000000000000ll));
+            else if (qb[q] != 0) atomicAdd(acc_b + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
+        }
+    }
+}
+
+template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<float> &S, int vb, int nvb, int csize) {
+    const Parts<float> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const Geo geo = S.geo;
+    const int off = S.d->off, np = S.d->np;
+    const long long shift = S.d->shift;
+    const int2 rg = slot_range(np, vb, nvb, csize);   // begin is even: chunks are multiples of TPB
+    const int begin = rg.x, end = rg.y;
+    int k = begin + 2 * threadIdx.x;
+    PPos cur = load_pos(P, k, end);
+    for (int base = begin; base < end; base += 2 * TPB, k += 2 * TPB) {
+        const PMom m = load_mom(P, k, end);
+        const PPos nxt = load_pos(P, k + 2 * TPB, end);   // prefetch
+        const AOut<float> a = a_particle<float>(S, geo, off, shift, cur.ix.x, cur.ox.x, cur.y.x, cur.z.x,
+                                                m.px.x, m.py.x, m.pz.x, m.w.x);
+        const AOut<float> b = a_particle<float>(S, geo, off, shift, cur.ix.y, cur.ox.y, cur.y.y, cur.z.y,
+                                                m.px.y, m.py.y, m.pz.y, m.w.y);
+        const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
+        if (la && lb) {
+            *reinterpret_cast<float2 *>(P.px + k) = make_float2(a.px, b.px);
+            *reinterpret_cast<float2 *>(P.py + k) = make_float2(a.py, b.py);
+            *reinterpret_cast<float2 *>(P.pz + k) = make_float2(a.pz, b.pz);
+        } else {
+            if (la) { P.px[k] = a.px; P.py[k] = a.py; P.pz[k] = a.pz; }
+            if (lb) { P.px[k + 1] = b.px; P.py[k + 1] = b.py; P.pz[k + 1] = b.pz; }
+        }
+        const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
+        const int o[4] = {0, geo.P, 1, geo.P + 1};
+        pair_deposit<1>(a.key, b.key, a.v, b.v, bnd, S.f.chi + a.b, S.f.chi + b.b, o);
+        cur = nxt;
+    }
+}
+
+template <class R> __global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_a(SimDev<R> S) {
     pass_a_body<R>(S, blockIdx.x, gridDim.x, 0);
 }
 
@@ -476,7 +644,7 @@ __device__ __forceinline__ int next_item(int *ticket) {
     return w;
 }
 template <class R>
-__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 5 : 3) k_pass_a_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n, int *ticket) {
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 4 : 3) k_pass_a_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n, int *ticket) {
     for (int w = next_item(ticket); w < n; w = next_item(ticket)) {
         const int4 it = items[w];
         pass_a_body<R>(pk.v[it.x], it.y, it.z, it.w);
