@@ -340,11 +340,10 @@ __device__ __forceinline__ PMom load_mom(const Parts<float> &P, int k, int lim) 
 
 // Deposit of a warp's 64 elements (see above); v*[q] belong to group q*M/4 with bounds
 // bnd[m] >= |value| over both elements.
-// Node q of an element with cell base b is acc[b + o[q]], o = {0, P, 1, P + 1} (chi) or
-// {0, 1, P0, P0 + P} with the caller's offsets.
+// Value q of an element with cell base b goes to base[q][b + o[q]].
 template <int M>
 __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const float (&va)[4], const float (&vb)[4],
-                                             const float (&bnd)[M], double *acc_a, double *acc_b,
+                                             const float (&bnd)[M], int ba, int bb, double *const (&base)[4],
                                              const int (&o)[4]) {
     const int lane = threadIdx.x & 31;
     int qa[4], qb[4], ec[M];
@@ -396,12 +395,12 @@ __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const flo
     for (int q = 0; q < 4; q++) {
         const int m = q * M / 4;
         if (dep_a) {
-            if (bad[m]) atomicAdd(acc_a + o[q], __longlong_as_double(0x7ff8000000000000ll));
-            else if (qa[q] != 0) atomicAdd(acc_a + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
+            if (bad[m]) atomicAdd(base[q] + ba + o[q], __longlong_as_double(0x7ff8000000000000ll));
+            else if (qa[q] != 0) atomicAdd(base[q] + ba + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
         }
         if (dep_b) {
-            if (bad[m]) atomicAdd(acc_b + o[q], __longlong_as_double(0x7ff8000000000000ll));
-            else if (qb[q] != 0) atomicAdd(acc_b + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
+            if (bad[m]) atomicAdd(base[q] + bb + o[q], __longlong_as_double(0x7ff8000000000000ll));
+            else if (qb[q] != 0) atomicAdd(base[q] + bb + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
         }
     }
 }
@@ -432,8 +431,9 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
             if (lb) { P.px[k + 1] = b.px; P.py[k + 1] = b.py; P.pz[k + 1] = b.pz; }
         }
         const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
+        double *const base_q[4] = {S.f.chi, S.f.chi, S.f.chi, S.f.chi};
         const int o[4] = {0, geo.P, 1, geo.P + 1};
-        pair_deposit<1>(a.key, b.key, a.v, b.v, bnd, S.f.chi + a.b, S.f.chi + b.b, o);
+        pair_deposit<1>(a.key, b.key, a.v, b.v, bnd, a.b, b.b, base_q, o);
         cur = nxt;
     }
 }
@@ -452,7 +452,7 @@ template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base,
 }
 
 // Cell-crossing particles of one warp, parked until the warp can process 32 of them at once.
-constexpr int QW = 64;                 // entries per warp (at most 32 join per iteration)
+constexpr int QW = 64;                 // entries per warp (at most 32 join per enqueue; drained at 32)
 constexpr int NWARP = TPB / 32;
 template <class R> struct CrossQueue {
     int ia[NWARP][QW], ja[NWARP][QW], di[NWARP][QW], dj[NWARP][QW];
@@ -518,6 +518,110 @@ __device__ __forceinline__ void drain_queue(const SimDev<R> &S, int off, CrossQu
 // cent) are queued per warp in shared memory and take the 3x3 general form 32 at a time, so
 // that their slow path runs on full warps.  Particles leaving the next step's window (x < 0,
 // x >= Nx dx) or reaching r >= r_max are marked dead after their deposit.
+// Results of pass B for one particle.
+template <class R> struct BOut {
+    unsigned key;              // b for a particle that stays in its cell, else kNoKey
+    int b;                     // its cell base (window-relative node index)
+    R v[4], bnd[2];            // Jx(i+1/2, j), Jx(i+1/2, j+1), Jr(i, j+1/2), Jr(i+1, j+1/2)
+    bool cross;                // alive and leaving its cell: the general deposit
+    int ia, ja, di, dj;        // the move, in cells
+    R fa, fb, fra, frb;        // in-cell fractions before and after
+    int ixn;                   // new lab cell (kDead when the particle leaves)
+    R ox1, y1, z1;
+};
+
+template <class R>
+__device__ __forceinline__ BOut<R> b_particle(const SimDev<R> &S, const Geo &geo, int off, long long shift,
+                                              int snext, int ix, R ox, R y, R z, R px, R py, R pz, R w) {
+    const R dt = S.k.dt, idr = S.k.idr, dtdx = S.k.dtdx;
+    const R rmax = S.k.rmax;
+    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
+    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
+    const bool alive = ix != kDead;
+    const int irel = (int)((long long)ix - shift);
+    const R r0 = sqrt_<R>(y * y + z * z);
+    const R rn0 = r0 * idr;
+    const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
+    const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
+    const R ig = rsqrt_<R>((R)1 + px * px + py * py + pz * pz + ph);   // 1/gbar
+    // The current is a difference of shape factors at two nearby positions: move x as
+    // an in-cell offset, and take the new radius as r^n plus the radial step in the
+    // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
+    R ox1 = ox + dtdx * px * ig;
+    const R dy = dt * py * ig, dz = dt * pz * ig;
+    const R y1 = y + dy, z1 = z + dz;
+    // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
+    // keep the 3-node shape window in range for non-finite input
+    int di = min(max(floor_int<R>(ox1), -1), 1);
+    ox1 -= (R)di;
+    if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
+    const int ia = L.ip;
+    const R r1 = sqrt_<R>(y1 * y1 + z1 * z1);
+    const R rsum = r0 + r1;
+    const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
+    R rn1 = rn0 + step_r * idr;
+    rn1 = rn1 < (R)0 ? (R)0 : rn1;
+    const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
+    const R fra = L.gp, frb = rn1 - (R)jb;
+    const bool stays = di == 0 && ja == jb;
+
+    BOut<R> o;
+    const R ddx = ox1 - ox, ddr = frb - fra;
+    const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
+    const bool fast = alive && stays;
+    const R bx = fast ? w * ddx : (R)0, br = fast ? w * ddr : (R)0;
+    // row factors 1/(dt A_j) of the two x faces and 1/(dt 2 pi r_{j+1/2} dx) of the r face
+    const R fx0 = tjx[ja], fx1 = tjx[ja + 1], fr = tjr[ja];
+    const R cx = -bx, cr = -br * fr;
+    o.v[0] = cx * ((R)1 - rbar) * fx0;
+    o.v[1] = cx * rbar * fx1;
+    o.v[2] = cr * ((R)1 - xbar);
+    o.v[3] = cr * xbar;
+    o.bnd[0] = fabs_<R>(bx) * (fx0 > fx1 ? fx0 : fx1);
+    o.bnd[1] = fabs_<R>(cr);
+    o.b = geo.at(off, ia, ja);
+    o.key = fast ? (unsigned)o.b : kNoKey;
+    o.cross = alive && !stays;
+    o.ia = ia; o.ja = ja; o.di = di; o.dj = jb - ja;
+    o.fa = ox; o.fb = ox1; o.fra = fra; o.frb = frb;
+    const int irel_next = ia + di - snext;
+    const bool dead = irel_next < 0 || irel_next >= geo.nx || r1 >= rmax;
+    o.ixn = dead ? kDead : ix + di;
+    o.ox1 = ox1; o.y1 = y1; o.z1 = z1;
+    return o;
+}
+
+// Park this warp's crossing moves in the queue (queued: same value on every lane).
+template <class R>
+__device__ __forceinline__ void enqueue_cross(CrossQueue<R> &Q, int wq, int &queued, const BOut<R> &o, R w) {
+    const int lane = threadIdx.x & 31;
+    const unsigned cm = __ballot_sync(FULL, o.cross);
+    if (o.cross) {
+        const int slot = queued + __popc(cm & ((1u << lane) - 1u));
+        Q.ia[wq][slot] = o.ia; Q.ja[wq][slot] = o.ja; Q.di[wq][slot] = o.di; Q.dj[wq][slot] = o.dj;
+        Q.fa[wq][slot] = o.fa; Q.fb[wq][slot] = o.fb; Q.fra[wq][slot] = o.fra; Q.frb[wq][slot] = o.frb;
+        Q.w[wq][slot] = w;
+    }
+    queued += __popc(cm);
+}
+
+// Diagnostic only (a separate instantiation): charge change q w (S1 - S0), general form.
+template <class R>
+__device__ __forceinline__ void charge_change(const SimDev<R> &S, const Geo &geo, int off, const BOut<R> &o, R w) {
+    const int ib = o.ia + o.di, jb = o.ja + o.dj, imin = min(o.ia, ib), jmin = min(o.ja, jb);
+    R s0x[3], s1x[3], s0r[3], s1r[3];
+    shape3<R>(o.ia, o.fa, imin, s0x);
+    shape3<R>(ib, o.fb, imin, s1x);
+    shape3<R>(o.ja, o.fra, jmin, s0r);
+    shape3<R>(jb, o.frb, jmin, s1r);
+    const int bb = geo.at(off, imin, jmin);
+#pragma unroll
+    for (int cc = 0; cc < 3; cc++)
+#pragma unroll
+        for (int l = 0; l < 3; l++)
+            atom_add(S.f.dq + bb + cc * geo.P + l, -(double)w * (double)(s1x[cc] * s1r[l] - s0x[cc] * s0r[l]));
+}
+
 template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const SimDev<R> &S, int vb, int nvb, int csize) {
     __shared__ CrossQueue<R> Q;
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
@@ -525,11 +629,7 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
     const int off = S.d->off, np = S.d->np;
     const long long shift = S.d->shift, step = S.d->step;
     const int snext = window_shifts(S.ph, step, shift) ? 1 : 0;
-    const R dt = S.k.dt, idr = S.k.idr, dtdx = S.k.dtdx;
-    const R rmax = S.k.rmax;
-    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
-    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
-    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int wq = threadIdx.x >> 5;
     int queued = 0;   // same value on every lane of the warp
     // each block walks one contiguous chunk of slots (see pass A)
     const int2 rg = slot_range(np, vb, nvb, csize);
@@ -538,86 +638,20 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
     PReg<R> cur = load_particle<R>(P, k, end);
     for (int base = begin; base < end; base += TPB, k += TPB) {
         const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
+        const BOut<R> o = b_particle<R>(S, geo, off, shift, snext, cur.ix, cur.ox, cur.y, cur.z, cur.px,
+                                        cur.py, cur.pz, cur.w);
+        enqueue_cross<R>(Q, wq, queued, o, cur.w);
         const bool alive = cur.ix != kDead;
-        const int ix = cur.ix;
-        const int irel = (int)((long long)ix - shift);
-        const R ox = cur.ox, y = cur.y, z = cur.z, w = cur.w;
-        const R px = cur.px, py = cur.py, pz = cur.pz;
-        const R r0 = sqrt_<R>(y * y + z * z);
-        const R rn0 = r0 * idr;
-        const Loc<R> L = locate<R>(irel, ox, rn0, geo.nx, geo.nr);
-        const R ph = gather4<R>(S.f.phih, geo, off, L.ip, L.fp, L.jp, L.gp, false);
-        const R ig = rsqrt_<R>((R)1 + px * px + py * py + pz * pz + ph);   // 1/gbar
-        // The current is a difference of shape factors at two nearby positions: move x as
-        // an in-cell offset, and take the new radius as r^n plus the radial step in the
-        // cancellation-free form (dy (y0+y1) + dz (z0+z1)) / (r0 + r1).
-        R ox1 = ox + dtdx * px * ig;
-        const R dy = dt * py * ig, dz = dt * pz * ig;
-        const R y1 = y + dy, z1 = z + dz;
-        // a particle moves less than one cell per step (dt < dx, dt < dr); the clamps only
-        // keep the 3-node shape window in range for non-finite input
-        int di = min(max(floor_int<R>(ox1), -1), 1);
-        ox1 -= (R)di;
-        if (ox1 >= (R)1) { ox1 -= (R)1; di = min(di + 1, 1); }
-        const int ia = L.ip;
-        const R r1 = sqrt_<R>(y1 * y1 + z1 * z1);
-        const R rsum = r0 + r1;
-        const R step_r = rsum > (R)0 ? (dy * (y + y1) + dz * (z + z1)) / rsum : (R)0;
-        R rn1 = rn0 + step_r * idr;
-        rn1 = rn1 < (R)0 ? (R)0 : rn1;
-        const int ja = L.jp, jb = min(max((int)rn1, ja - 1), ja + 1);
-        const R fra = L.gp, frb = rn1 - (R)jb;
-        const bool stays = di == 0 && ja == jb;
-
-        const R ddx = ox1 - ox, ddr = frb - fra;
-        const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
-        const bool fast = alive && stays;
-        const R bx = fast ? w * ddx : (R)0, br = fast ? w * ddr : (R)0;
-        // row factors 1/(dt A_j) of the two x faces and 1/(dt 2 pi r_{j+1/2} dx) of the r face
-        const R fx0 = tjx[ja], fx1 = tjx[ja + 1], fr = tjr[ja];
-        const R cx = -bx, cr = -br * fr;
-        const R v[4] = {cx * ((R)1 - rbar) * fx0, cx * rbar * fx1, cr * ((R)1 - xbar), cr * xbar};
-        const R bnd[2] = {fabs_<R>(bx) * (fx0 > fx1 ? fx0 : fx1), fabs_<R>(cr)};
-        const int b = geo.at(off, ia, ja);
-        const unsigned key = fast ? (unsigned)b : kNoKey;
-
-        // queue the crossing moves in this warp's slots
-        const bool cross = alive && !stays;
-        const unsigned cm = __ballot_sync(FULL, cross);
-        if (cross) {
-            const int slot = queued + __popc(cm & ((1u << lane) - 1u));
-            Q.ia[wq][slot] = ia; Q.ja[wq][slot] = ja; Q.di[wq][slot] = di; Q.dj[wq][slot] = jb - ja;
-            Q.fa[wq][slot] = ox; Q.fb[wq][slot] = ox1; Q.fra[wq][slot] = fra; Q.frb[wq][slot] = frb;
-            Q.w[wq][slot] = w;
-        }
-        queued += __popc(cm);
-        // diagnostic only (a separate instantiation): charge change q w (S1 - S0), general form
-        if (DQ && alive) {
-            const int ib = ia + di, imin = min(ia, ib), jmin = min(ja, jb);
-            R s0x[3], s1x[3], s0r[3], s1r[3];
-            shape3<R>(ia, ox, imin, s0x);
-            shape3<R>(ib, ox1, imin, s1x);
-            shape3<R>(ja, fra, jmin, s0r);
-            shape3<R>(jb, frb, jmin, s1r);
-            const int bb = geo.at(off, imin, jmin);
-#pragma unroll
-            for (int cc = 0; cc < 3; cc++)
-#pragma unroll
-                for (int l = 0; l < 3; l++)
-                    atom_add(S.f.dq + bb + cc * geo.P + l,
-                             -(double)w * (double)(s1x[cc] * s1r[l] - s0x[cc] * s0r[l]));
-        }
+        if (DQ && alive) charge_change<R>(S, geo, off, o, cur.w);
         if (alive) {
-            const int irel_next = ia + di - snext;
-            const bool dead = irel_next < 0 || irel_next >= geo.nx || r1 >= rmax;
-            P.ix[k] = dead ? kDead : ix + di;
-            P.ox[k] = ox1;
-            P.y[k] = y1;
-            P.z[k] = z1;
+            P.ix[k] = o.ixn;
+            P.ox[k] = o.ox1;
+            P.y[k] = o.y1;
+            P.z[k] = o.z1;
         }
-        const Run run = run_of(key);
-        double *const addr[4] = {S.f.jx + b, S.f.jx + b + 1, S.f.jr + b, S.f.jr + b + geo.P};
-        run_deposit<2>(run, key, v, bnd, addr);
+        const Run run = run_of(o.key);
+        double *const addr[4] = {S.f.jx + o.b, S.f.jx + o.b + 1, S.f.jr + o.b, S.f.jr + o.b + geo.P};
+        run_deposit<2>(run, o.key, o.v, o.bnd, addr);
         // at most 32 join per iteration, so draining at 32 keeps the queue within QW
         if (queued >= 32) {
             drain_queue<R>(S, off, Q, wq, queued);
@@ -626,6 +660,58 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
         cur = nxt;
     }
     drain_queue<R>(S, off, Q, wq, queued);
+}
+
+// FP32: two neighbouring particles per thread, as in pass A; the crossing moves of each half
+// join the queue in turn (draining at 32 after each keeps it within QW).
+template <>
+__device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S, int vb, int nvb, int csize) {
+    __shared__ CrossQueue<float> Q;
+    const Parts<float> P = S.d->pbuf ? S.p[1] : S.p[0];
+    const Geo geo = S.geo;
+    const int off = S.d->off, np = S.d->np;
+    const long long shift = S.d->shift, step = S.d->step;
+    const int snext = window_shifts(S.ph, step, shift) ? 1 : 0;
+    const int wq = threadIdx.x >> 5;
+    int queued = 0;   // same value on every lane of the warp
+    const int2 rg = slot_range(np, vb, nvb, csize);   // begin is even: chunks are multiples of TPB
+    const int begin = rg.x, end = rg.y;
+    int k = begin + 2 * threadIdx.x;
+    PPos cur = load_pos(P, k, end);
+    for (int base = begin; base < end; base += 2 * TPB, k += 2 * TPB) {
+        const PMom m = load_mom(P, k, end);
+        const PPos nxt = load_pos(P, k + 2 * TPB, end);   // prefetch
+        const BOut<float> a = b_particle<float>(S, geo, off, shift, snext, cur.ix.x, cur.ox.x, cur.y.x,
+                                                cur.z.x, m.px.x, m.py.x, m.pz.x, m.w.x);
+        const BOut<float> b = b_particle<float>(S, geo, off, shift, snext, cur.ix.y, cur.ox.y, cur.y.y,
+                                                cur.z.y, m.px.y, m.py.y, m.pz.y, m.w.y);
+        enqueue_cross<float>(Q, wq, queued, a, m.w.x);
+        if (queued >= 32) {
+            drain_queue<float>(S, off, Q, wq, queued);
+            queued = 0;
+        }
+        enqueue_cross<float>(Q, wq, queued, b, m.w.y);
+        const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
+        if (la && lb) {
+            *reinterpret_cast<int2 *>(P.ix + k) = make_int2(a.ixn, b.ixn);
+            *reinterpret_cast<float2 *>(P.ox + k) = make_float2(a.ox1, b.ox1);
+            *reinterpret_cast<float2 *>(P.y + k) = make_float2(a.y1, b.y1);
+            *reinterpret_cast<float2 *>(P.z + k) = make_float2(a.z1, b.z1);
+        } else {
+            if (la) { P.ix[k] = a.ixn; P.ox[k] = a.ox1; P.y[k] = a.y1; P.z[k] = a.z1; }
+            if (lb) { P.ix[k + 1] = b.ixn; P.ox[k + 1] = b.ox1; P.y[k + 1] = b.y1; P.z[k + 1] = b.z1; }
+        }
+        const float bnd[2] = {a.bnd[0] > b.bnd[0] ? a.bnd[0] : b.bnd[0], a.bnd[1] > b.bnd[1] ? a.bnd[1] : b.bnd[1]};
+        double *const base_q[4] = {S.f.jx, S.f.jx, S.f.jr, S.f.jr};
+        const int o[4] = {0, 1, 0, geo.P};
+        pair_deposit<2>(a.key, b.key, a.v, b.v, bnd, a.b, b.b, base_q, o);
+        if (queued >= 32) {
+            drain_queue<float>(S, off, Q, wq, queued);
+            queued = 0;
+        }
+        cur = nxt;
+    }
+    drain_queue<float>(S, off, Q, wq, queued);
 }
 
 template <class R, bool DQ>
