@@ -419,19 +419,13 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
     for (int base = begin; base < end; base += 2 * TPB, k += 2 * TPB) {
         const PMom m = load_mom(P, k, end);
         const PPos nxt = load_pos(P, k + 2 * TPB, end);   // prefetch
+        const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
         const AOut<float> a = a_particle<float>(S, geo, off, shift, cur.ix.x, cur.ox.x, cur.y.x, cur.z.x,
                                                 m.px.x, m.py.x, m.pz.x, m.w.x);
+        if (la) { __stcs(P.px + k, a.px); __stcs(P.py + k, a.py); __stcs(P.pz + k, a.pz); }
         const AOut<float> b = a_particle<float>(S, geo, off, shift, cur.ix.y, cur.ox.y, cur.y.y, cur.z.y,
                                                 m.px.y, m.py.y, m.pz.y, m.w.y);
-        const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
-        if (la && lb) {
-            __stcs(reinterpret_cast<float2 *>(P.px + k), make_float2(a.px, b.px));
-            __stcs(reinterpret_cast<float2 *>(P.py + k), make_float2(a.py, b.py));
-            __stcs(reinterpret_cast<float2 *>(P.pz + k), make_float2(a.pz, b.pz));
-        } else {
-            if (la) { P.px[k] = a.px; P.py[k] = a.py; P.pz[k] = a.pz; }
-            if (lb) { P.px[k + 1] = b.px; P.py[k + 1] = b.py; P.pz[k + 1] = b.pz; }
-        }
+        if (lb) { __stcs(P.px + k + 1, b.px); __stcs(P.py + k + 1, b.py); __stcs(P.pz + k + 1, b.pz); }
         const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
         double *const base_q[4] = {S.f.chi, S.f.chi, S.f.chi, S.f.chi};
         const int o[4] = {0, geo.P, 1, geo.P + 1};
