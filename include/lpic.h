@@ -170,6 +170,16 @@ lpic_status lpic_step(lpic_ctx *ctx, int nsteps);
 lpic_status lpic_diagnose(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, size_t cap,
                           size_t *written);
 
+/* Asynchronous form of lpic_diagnose for the on-axis wake (LPIC_DIAG_EX_AXIS, same layout:
+ * Nx doubles): enqueues the read into host_out on the context stream and returns without
+ * synchronising, so that a caller can consume step n's wake while step n+1 runs.  host_out
+ * should be page-locked (a pageable destination makes the copy synchronous); it holds the
+ * result once the stream has passed this call (an event recorded after it, or any
+ * synchronising call) and must stay valid until then.  Errors: LPIC_EINVAL for another kind
+ * or a NULL host_out, LPIC_EBUFSIZE if cap < Nx * 8; device-side errors of earlier steps are
+ * reported by the next synchronising call. */
+lpic_status lpic_diagnose_async(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, size_t cap);
+
 /* Overwrite a part of the state from host memory in the dump layout of the same kind
  * (checkpoint restore, or starting from another implementation's state).  Accepts
  * LPIC_DIAG_EX/ER/BT/A/AM (exact sizes), LPIC_DIAG_PARTICLES (7n doubles: replaces the

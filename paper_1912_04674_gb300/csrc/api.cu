@@ -637,6 +637,19 @@ lpic_status lpic_step(lpic_ctx *c, int nsteps) {
     return LPIC_OK;
 }
 
+lpic_status lpic_diagnose_async(lpic_ctx *c, lpic_diag_kind kind, void *host_out, size_t cap) {
+    if (!c) return LPIC_EINVAL;
+    if (kind != LPIC_DIAG_EX_AXIS || !host_out)
+        return c->fail(LPIC_EINVAL, "lpic_diagnose_async: LPIC_DIAG_EX_AXIS into a non-NULL buffer only");
+    const size_t n = (size_t)c->geo.nx * sizeof(double);
+    if (cap < n) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+    // the staging area is reused only by later work on the same stream, after this copy
+    c->dispatch([&](auto &S) { launch_diag_ex_axis(S, (double *)c->stage, c->st); });
+    cudaError_t e = cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_diagnose_async");
+}
+
 lpic_status lpic_diagnose(lpic_ctx *c, lpic_diag_kind kind, void *host_out, size_t cap,
                           size_t *written) {
     if (!c) return LPIC_EINVAL;

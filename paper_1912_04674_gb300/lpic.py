@@ -69,6 +69,7 @@ _SIGS = {
     "lpic_load_plasma": (C.c_int, [C.c_void_p, C.POINTER(lpic_plasma_params)]),
     "lpic_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lpic_diagnose": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "lpic_diagnose_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "lpic_upload": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "lpic_set_kernel_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lpic_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
@@ -150,6 +151,10 @@ def lpic_diagnose(ctx, kind: int, host_ptr, cap: int) -> int:
     written = C.c_size_t(0)
     _check(lib().lpic_diagnose(ctx, int(kind), host_ptr, cap, C.byref(written)), ctx)
     return int(written.value)
+
+
+def lpic_diagnose_async(ctx, kind: int, host_ptr, cap: int):
+    _check(lib().lpic_diagnose_async(ctx, int(kind), host_ptr, cap), ctx)
 
 
 def lpic_diagnose_size(ctx, kind: int) -> int:
@@ -400,6 +405,14 @@ class Simulation:
     def ex_axis(self) -> np.ndarray:
         return self._diag("ex_axis", np.float64, self.grid.nx)
 
+    def ex_axis_async(self, out: np.ndarray):
+        """Enqueue the on-axis wake read into `out` (Nx float64, page-locked, e.g. from a
+        pinned torch tensor) on this simulation's stream; `out` holds it once the stream has
+        passed this point (record an event on self.stream after the call)."""
+        if out.dtype != np.float64 or out.size < self.grid.nx or not out.flags.c_contiguous:
+            raise LpicError(1, "ex_axis_async: out must be a contiguous float64 array of Nx values")
+        lpic_diagnose_async(self.ctx, DIAG["ex_axis"], out.ctypes.data_as(C.c_void_p), out.nbytes)
+
     def a_abs_max(self) -> float:
         return float(self._diag("a_abs_max", np.float64, 1)[0])
 
@@ -442,19 +455,27 @@ class Simulation:
 
     # -- uploads -----------------------------------------------------------------------------
     def upload_field(self, name: str, arr: np.ndarray):
-        a = np.ascontiguousarray(arr)
+        a = np.ascontiguousarray(arr)       # no copy of a contiguous array of the right type
         if name in ("a", "am"):
-            a = np.ascontiguousarray(a.astype(np.complex128)).view(np.float64)
+            a = np.ascontiguousarray(a.astype(np.complex128, copy=False)).view(np.float64)
         else:
-            a = a.astype(np.float64)
+            a = a.astype(np.float64, copy=False)
         lpic_upload(self.ctx, DIAG[name], a.ctypes.data_as(C.c_void_p), a.nbytes)
 
     def upload_particles(self, parts: dict):
         n = len(parts["x"])
         raw = np.concatenate([np.asarray(parts[k], dtype=np.float64) for k in PART_COMPONENTS]) if n else np.zeros(0)
+        self.upload_particles_raw(raw, parts.get("id") if n else None)
+
+    def upload_particles_raw(self, raw: np.ndarray, ids: np.ndarray | None = None):
+        """Replace the particle set from one contiguous float64 array of 7n values in the
+        dump layout (x, y, z, px, py, pz, w blocks), and optionally its n ids; no host copy
+        is made, so a page-locked `raw` is copied to the device at full link speed."""
+        if raw.dtype != np.float64 or not raw.flags.c_contiguous or raw.size % 7:
+            raise LpicError(1, "upload_particles_raw: contiguous float64 array of 7n values expected")
         lpic_upload(self.ctx, DIAG["particles"], raw.ctypes.data_as(C.c_void_p), raw.nbytes)
-        if "id" in parts and n:
-            ids = np.ascontiguousarray(parts["id"], dtype=np.uint64)
+        if ids is not None and raw.size:
+            ids = np.ascontiguousarray(ids, dtype=np.uint64)
             lpic_upload(self.ctx, DIAG["particle_ids"], ids.ctypes.data_as(C.c_void_p), ids.nbytes)
 
     def inject_bunch(self, parts: dict, gamma: float):

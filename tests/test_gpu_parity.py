@@ -153,3 +153,23 @@ def test_window_slide_relocation_matches_oracle():
         g.step(10)
         assert_parity(o, g, tol=1e-9)
     assert o.shift >= 60
+
+
+def test_async_wake_read_matches_the_synchronising_read():
+    """lpic_diagnose_async: the wake enqueued into pinned host memory after a step is the one
+    lpic_diagnose returns for that step; a short buffer is refused."""
+    import torch
+
+    g = gpu_from(C1, precision="fp32")
+    held = torch.zeros(C1.nx, dtype=torch.float64).pin_memory()
+    buf = held.numpy()
+    for _ in range(3):
+        g.step(5)
+        g.ex_axis_async(buf)
+        ev = torch.cuda.Event()
+        ev.record(g.stream)
+        ev.synchronize()
+        np.testing.assert_array_equal(buf, g.ex_axis())
+    assert np.abs(buf).max() > 0
+    with pytest.raises(Exception):
+        g.ex_axis_async(np.zeros(3))
