@@ -274,7 +274,7 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps_per_ctx);
  *   multiple of 256 in [1024, 1048576]; default 4096).  Smaller items balance the blocks
  *   better, larger ones cost less per item.
  * packs: split the simulations into this many packs (0: as few as the parameter space
- *   allows, one per 48 simulations), each with its own launch sequence as a parallel branch
+ *   allows, one per 46 simulations), each with its own launch sequence as a parallel branch
  *   of the graph, so that phases of different packs overlap on the device.  -1: no fused
  *   launches; each step replays every simulation's own step graph (lpic_step) on its own
  *   stream, in turn, which overlaps better for batches of large simulations.

@@ -91,7 +91,7 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
 }
 
 struct Layout {
-    size_t desc, tab, grid[17], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
+    size_t desc, tab, grid[18], parts[2][9], key, count, blocksum, blockcnt, icount, diag, stage, total;
     int P, nlive, ncol;
 };
 
@@ -106,14 +106,18 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
     L.desc = take(sizeof(Desc));
     L.tab = take((size_t)NTAB * L.P * rs);
-    // ex er bt btn phih (R), pg (4R), [unused 6, 7], a0 a1 (2R), chi jx jr dq (double)
+    // ex er bt btn phih (R), pg (4R), exq erq (2R, FP32 only), a0 a1 (2R), chi jx jr dq
+    // (double), [14-16 filter], btq (2R, FP32 only)
+    const bool paired = prec != LPIC_FP64;
     for (int k = 0; k < 5; k++) L.grid[k] = take(cells * rs);
     L.grid[5] = take(cells * 4 * rs);
-    L.grid[6] = L.grid[7] = 0;
+    L.grid[6] = paired ? take(cells * 2 * rs) : 0;
+    L.grid[7] = paired ? take(cells * 2 * rs) : 0;
     for (int k = 8; k < 10; k++) L.grid[k] = take(cells * 2 * rs);
     for (int k = 10; k < 14; k++) L.grid[k] = take(cells * 8);
     // filtered current and charge change (only with the binomial filter on)
     for (int k = 14; k < 17; k++) L.grid[k] = g->filter_passes > 0 ? take(cells * 8) : 0;
+    L.grid[17] = paired ? take(cells * 2 * rs) : 0;
     const size_t cap = (size_t)g->particle_capacity;
     for (int b = 0; b < 2; b++) {
         L.parts[b][0] = take(cap * 4);                          // ix
@@ -300,6 +304,10 @@ template <class R> void fill_views(lpic_ctx *c, SimDev<R> &S) {
     S.f.btn = (R *)(b + L.grid[3]);
     S.f.phih = (R *)(b + L.grid[4]);
     S.f.pg = (Q4<R> *)(b + L.grid[5]);
+    using CT = typename Cplx<R>::t;
+    S.f.exq = L.grid[6] ? (CT *)(b + L.grid[6]) : nullptr;
+    S.f.erq = L.grid[7] ? (CT *)(b + L.grid[7]) : nullptr;
+    S.f.btq = L.grid[17] ? (CT *)(b + L.grid[17]) : nullptr;
     S.f.a[0] = (typename Cplx<R>::t *)(b + L.grid[8]);
     S.f.a[1] = (typename Cplx<R>::t *)(b + L.grid[9]);
     S.f.chi = (double *)(b + L.grid[10]);

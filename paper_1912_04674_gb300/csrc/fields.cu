@@ -29,15 +29,36 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
     const long long id = g.at(off, i, j);
     const R dt = S.k.dt, idx_ = S.k.idx, idr = S.k.idr;
 
+    R btn_here = (R)0;
     if (i >= 0 && i < g.nx && j < g.nr) {
         R bold = S.f.bt[id];
         R dexdr = (S.f.ex[id + 1] - S.f.ex[id]) * idr;
         R derdx = (S.f.er[g.at(off, i + 1, j)] - S.f.er[id]) * idx_;
         R bnew = bold + dt * (dexdr - derdx);
         S.f.bt[id] = bnew;
-        S.f.btn[id] = (R)0.5 * (bold + bnew);
-    } else {
-        S.f.btn[id] = (R)0;
+        btn_here = (R)0.5 * (bold + bnew);
+    }
+    S.f.btn[id] = btn_here;
+    if constexpr (sizeof(R) == 4) {
+        // radial pairs for the FP32 gathers (nodes i in [-1, nx+1], j in [-1, nr]).  E is not
+        // written by this kernel, so a thread reads its upper neighbour; B is updated in place,
+        // so B^n of node (i, j) is stored by its own thread into both records that hold it:
+        // (i, j).x and (i, j-1).y (separate 4-byte words, no two threads write the same one).
+        if (i >= -1 && i <= g.nx + 1 && j <= g.nr + 1) {
+            float *bq = reinterpret_cast<float *>(S.f.btq);
+            bq[2 * (long long)id] = btn_here;
+            bq[2 * (long long)id - 1] = btn_here;   // (i, j-1).y; for j = 0 that of row -1
+            if (j <= g.nr) {
+                const R ex0 = S.f.ex[id], er0 = S.f.er[id];
+                S.f.exq[id] = make_float2(ex0, S.f.ex[id + 1]);
+                S.f.erq[id] = make_float2(er0, S.f.er[id + 1]);
+                if (j == 0) {   // row -1: the odd mirror (read for Er and Btheta only)
+                    S.f.exq[id - 1] = make_float2(-ex0, ex0);
+                    S.f.erq[id - 1] = make_float2(-er0, er0);
+                    bq[2 * (long long)id - 2] = -btn_here;
+                }
+            }
+        }
     }
 
     Q4<R> q4;

@@ -64,6 +64,11 @@ template <class R> struct Fields {
     typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
     R *btn, *phih;                   // per step: B^n, Phi^{n+1/2}
     Q4<R> *pg;                       // per step: (Phi^n, dPhi/dx, dPhi/dr)
+    // per step, FP32 contexts only (else null): E^n and B^n as pairs of radial neighbours,
+    // element (i, j) = (F(i, j), F(i, j+1)), so that a gather reads two 8-byte records; the
+    // element of row -1 (the spare last row of the previous column) is (-F(i, 0), F(i, 0)),
+    // the odd mirror of Er and Btheta across the axis
+    typename Cplx<R>::t *exq, *erq, *btq;
     double *chi, *jx, *jr, *dq;      // per step FP64 accumulators (deposit targets)
     // the current (and charge change) the fields see: the deposit targets, or, with the
     // binomial filter on, separate arrays the filter writes from them
@@ -301,8 +306,8 @@ int bunch_solve_and_add(const SimDev<R> &S, int k0, int n, double gamma, void *s
 // The views of the simulations of one fused launch travel by value in the kernel's
 // parameter space (a __grid_constant__ pack, read through the constant cache like a single
 // simulation's view, so the bodies keep the register budget of the single kernels).
-// 48 views of at most 640 bytes plus the other arguments fit the 32,764-byte limit.
-constexpr int kPackMax = 48;
+// 46 views of at most 696 bytes plus the other arguments fit the 32,764-byte limit.
+constexpr int kPackMax = 46;
 template <class R> struct SimPack { SimDev<R> v[kPackMax]; };
 static_assert(sizeof(SimPack<double>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764 &&
                   sizeof(SimPack<float>) + 2 * sizeof(void *) + 2 * sizeof(int) <= 32764,

@@ -193,6 +193,15 @@ __device__ __forceinline__ int2 slot_range(int np, int vb, int nvb, int csize) {
     return make_int2(begin, min(begin + chunk, np));
 }
 
+// Gather from radial pairs (FP32 pass A): the same weights and the same sum as gather4, with
+// the two rows of a column in one 8-byte record; row -1 holds the odd mirror.
+__device__ __forceinline__ float gather_q(const float2 *__restrict__ G, const Geo &geo, int off, int i, float f,
+                                          int j, float gw) {
+    const int b = geo.at(off, i, j);
+    const float2 c0 = __ldg(G + b), c1 = __ldg(G + b + geo.P);
+    return (1.f - f) * (1.f - gw) * c0.x + f * (1.f - gw) * c1.x + (1.f - f) * gw * c0.y + f * gw * c1.y;
+}
+
 // Results of pass A for one particle: its susceptibility deposit (four primal nodes from b,
 // row factors applied, with a bound on their size) and its new momentum.
 template <class R> struct AOut {
@@ -202,7 +211,7 @@ template <class R> struct AOut {
     R px, py, pz;
 };
 
-template <class R>
+template <class R, bool PAIRED = false>
 __device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo, int off, long long shift,
                                               int ix, R ox, R y, R z, R px, R py, R pz, R w) {
     const R hdt = S.k.hdt, idr = S.k.idr;
@@ -215,9 +224,18 @@ __device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo
     const R ir = onaxis ? (R)0 : rsqrt_<R>(r2);
     const R r = r2 * ir, ct = onaxis ? (R)1 : y * ir, st = z * ir;
     const Loc<R> L = locate<R>(irel, ox, r * idr, geo.nx, geo.nr);
-    const R exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
-    const R erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
-    const R btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
+    R exg, erg, btg;
+    if constexpr (PAIRED) {
+        // live particles have id >= -1; the clamp keeps holes (irel = -1) in the arrays
+        const int id = L.id < -1 ? -1 : L.id;
+        exg = gather_q(S.f.exq, geo, off, id, L.fd, L.jp, L.gp);
+        erg = gather_q(S.f.erq, geo, off, L.ip, L.fp, L.jd, L.gd);
+        btg = gather_q(S.f.btq, geo, off, id, L.fd, L.jd, L.gd);
+    } else {
+        exg = gather4<R>(S.f.ex, geo, off, L.id, L.fd, L.jp, L.gp, false);
+        erg = gather4<R>(S.f.er, geo, off, L.ip, L.fp, L.jd, L.gd, true);
+        btg = gather4<R>(S.f.btn, geo, off, L.id, L.fd, L.jd, L.gd, true);
+    }
     // Phi, dPhi/dx, dPhi/dr share the primal weights: one 4-vector load per corner
     const int b = geo.at(off, L.ip, L.jp);
     const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
@@ -420,10 +438,10 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
         const PMom m = load_mom(P, k, end);
         const PPos nxt = load_pos(P, k + 2 * TPB, end);   // prefetch
         const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
-        const AOut<float> a = a_particle<float>(S, geo, off, shift, cur.ix.x, cur.ox.x, cur.y.x, cur.z.x,
+        const AOut<float> a = a_particle<float, true>(S, geo, off, shift, cur.ix.x, cur.ox.x, cur.y.x, cur.z.x,
                                                 m.px.x, m.py.x, m.pz.x, m.w.x);
         if (la) { __stcs(P.px + k, a.px); __stcs(P.py + k, a.py); __stcs(P.pz + k, a.pz); }
-        const AOut<float> b = a_particle<float>(S, geo, off, shift, cur.ix.y, cur.ox.y, cur.y.y, cur.z.y,
+        const AOut<float> b = a_particle<float, true>(S, geo, off, shift, cur.ix.y, cur.ox.y, cur.y.y, cur.z.y,
                                                 m.px.y, m.py.y, m.pz.y, m.w.y);
         if (lb) { __stcs(P.px + k + 1, b.px); __stcs(P.py + k + 1, b.py); __stcs(P.pz + k + 1, b.pz); }
         const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
