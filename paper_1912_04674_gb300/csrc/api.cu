@@ -1304,24 +1304,24 @@ lpic_status lpic_batch_step(lpic_batch *b, const int *steps) {
         // the batch stream; later work on the batch stream comes after all of them
         cudaEventRecord(b->ev, b->st);
         for (size_t k = 0; k < n; k++) cudaStreamWaitEvent(b->ctx[k]->st, b->ev, 0);
-        for (int t = 0; t < maxs; t++)
-            for (size_t k = 0; k < n; k++) {
+        lpic_status s = LPIC_OK;
+        for (int t = 0; t < maxs && s == LPIC_OK; t++)
+            for (size_t k = 0; k < n && s == LPIC_OK; k++) {
                 if (steps[k] <= t) continue;
                 lpic_ctx *c = b->ctx[k];
                 long long before = 0, after = 0;
                 for (int f = 0; f < lpic_ctx::kFamilies; f++) before += c->launches[f];
-                const lpic_status s = lpic_step(c, 1);
-                if (s != LPIC_OK) {
-                    b->err = "batch: simulation " + std::to_string(k) + ": " + c->err;
-                    return s;
-                }
+                s = lpic_step(c, 1);
+                if (s != LPIC_OK) b->err = "batch: simulation " + std::to_string(k) + ": " + c->err;
                 for (int f = 0; f < lpic_ctx::kFamilies; f++) after += c->launches[f];
                 b->launches += after - before;
             }
+        // also after a failed step: the batch stream waits for whatever was enqueued
         for (size_t k = 0; k < n; k++) {
             cudaEventRecord(b->ev, b->ctx[k]->st);
             cudaStreamWaitEvent(b->st, b->ev, 0);
         }
+        if (s != LPIC_OK) return s;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return LPIC_ECUDA; }
         return LPIC_OK;

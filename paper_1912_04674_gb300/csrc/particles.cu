@@ -106,7 +106,7 @@ template <class T, int N> __device__ __forceinline__ void run_sums(const Run &r,
     }
 }
 
-// q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 254): the integer converts
+// q * 2^(e - 151) in FP64, exactly (|q| < 2^31, q != 0, 25 <= e <= 255): the integer converts
 // to FP64 exactly (one conversion per value, issued by the run heads only), and the power of
 // two is added to its exponent field, which stays in the normal range for these q and e.
 // (Measured faster than assembling the bits with 32-bit integer operations.)
@@ -395,12 +395,12 @@ __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const flo
     const int head = 31 - __clz(starts & le);                      // first lane of this chain
     const int span = (int)__reduce_max_sync(FULL, (unsigned)(lane - head + 1));
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        if (o >= span) break;
-        const bool in = lane - o >= head;
+    for (int d = 1; d < 32; d <<= 1) {
+        if (d >= span) break;
+        const bool in = lane - d >= head;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int t = __shfl_up_sync(FULL, qb[q], o);
+            const int t = __shfl_up_sync(FULL, qb[q], d);
             if (in) qb[q] += t;
         }
     }
