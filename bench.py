@@ -71,6 +71,8 @@ def source_sha(paths) -> str:
     return h.hexdigest()[:16]
 
 
+METRIC = "particle-steps/s FP32 vs FP64 at <=1e-3 wake err; scan p50/p99 latency"
+
 KERNEL_SOURCES = {
     "pass_a": ["paper_1912_04674_gb300/csrc/particles.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
     "pass_b": ["paper_1912_04674_gb300/csrc/particles.cu", "paper_1912_04674_gb300/csrc/lpic_internal.cuh"],
@@ -625,7 +627,7 @@ def run_ours(args):
         r32, r64 = result["fp32"], result["fp64"]
         w = WORKLOAD
         line = {
-            "metric": "particle-steps/s FP32 vs FP64 at <=1e-3 wake err; scan p50/p99 latency",
+            "metric": METRIC,
             "value": r32["value"], "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -677,7 +679,7 @@ def run_reference(args):
     v = units / dt
     sample = f"{w.name}: {steps} of {args.steps} requested FP64 oracle timesteps (150 s cap), single thread"
     print(json.dumps({
-        "impl": "reference", "metric": "particle-steps/s FP32 vs FP64 at <=1e-3 wake err; scan p50/p99 latency",
+        "impl": "reference", "metric": METRIC,
         "value": v, "unit": "particle-steps/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
