@@ -248,13 +248,16 @@ const char *lpic_last_error(const lpic_ctx *ctx);
  * batch advances them together: one step is a fixed sequence of fused persistent launches
  * (prepass, pass A, envelope, pass B, Ampere, window), each walking a work list of
  * {simulation, tile or block of particle slots} items over every active simulation,
- * recorded once per set of active simulations in a CUDA graph and replayed.  Relocation
- * and the periodic counting sort stay per simulation, on the batch stream.
+ * recorded once per set of active simulations in a CUDA graph and replayed; the blocks of
+ * the particle passes draw their items from ticket counters.  The periodic counting sorts
+ * of the simulations due at a step are seven more fused launches in a second graph;
+ * relocation stays per simulation, on the batch stream.  A tuning (lpic_batch_set_tuning)
+ * can instead replay each simulation's own step graph.
  * All contexts must share one precision and one device, be initialised
  * (lpic_init_envelope done), and appear once.  The contexts keep their own buffers. */
 
-/* Device bytes the batch needs for its simulation views and work lists (0 if the
- * contexts are invalid).  Depends on the contexts' shapes and the device's SM count. */
+/* Device bytes the batch needs for its sort flags, item tickets and work lists (0 if the
+ * contexts are invalid).  Depends on the contexts' shapes. */
 size_t lpic_batch_required_bytes(lpic_ctx *const *ctxs, int n);
 
 /* device_buf: caller-owned, 256-byte aligned, at least lpic_batch_required_bytes bytes,
