@@ -280,6 +280,9 @@ class Batch:
         lpic_batch_step(self.b, steps)
 
     def set_tuning(self, particles_per_item: int, packs: int = 0):
+        """Work-item size of the fused particle passes and pack count (0: as few packs as the
+        launch parameter space allows; -1: no fused launches, each simulation's own step
+        graph in turn), effective at the next step."""
         lpic_batch_set_tuning(self.b, particles_per_item, packs)
 
     def launches(self) -> int:
