@@ -467,10 +467,13 @@ def filter_leg(steps: int = 200, settle_steps: int = 300, passes: int = 7):
             prof = kernel_profile(sim, 40)
             t = prof["filter"]["ms_avg"]
             nbytes = 16 * (w.nx * (w.nr + 1) + (w.nx + 1) * w.nr)
-            pk = peaks().get("hbm_gbs") or FALLBACK_HBM_GBS
+            pk, src = peaks().get("hbm_gbs"), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+            if not pk:
+                pk, src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s, one earlier GB300 measurement (of fallback)"
             out["filter_kernel"] = {"ms_per_launch": round(t, 4), "algorithmic_bytes": nbytes,
                                     "achieved_gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
-                                    "frac_of_measured_hbm": round(nbytes / (t * 1e-3) / 1e9 / pk, 4) if pk else None}
+                                    "frac_of_hbm_peak": round(nbytes / (t * 1e-3) / 1e9 / pk, 4),
+                                    "peak_source": src}
         sim.close()
         del sim
         torch.cuda.empty_cache()

@@ -50,7 +50,7 @@ typedef enum {
     LPIC_EBUFSIZE = 4,       /* output buffer too small, or particle capacity exceeded */
     LPIC_ECUDA = 5,          /* a CUDA runtime call failed                             */
     LPIC_ETIMEOUT = 6,       /* a bounded device wait gave up                          */
-    LPIC_ENONFINITE = 7,     /* a NaN/Inf was found by a diagnostic                    */
+    LPIC_ENONFINITE = 7,     /* a NaN/Inf: a diagnostic's result or a pushed position  */
     LPIC_ESTATE = 8          /* call out of order (e.g. step before init)              */
 } lpic_status;
 
@@ -161,12 +161,16 @@ lpic_status lpic_load_plasma(lpic_ctx *ctx, const lpic_plasma_params *plasma);
 /* Advance nsteps timesteps (paper Sec. 3, the 3D envelope loop order):
  * Faraday -> gather/chi deposit/ponderomotive Boris -> envelope solve (Eq. envelope_solver)
  * -> position push/charge-conserving current -> Ampere -> moving window/injection,
- * with a counting sort every sort_every steps.  Asynchronous on the context stream. */
+ * with a counting sort every sort_every steps.  Asynchronous on the context stream.
+ * Conditions the kernels latch (plasma injection beyond the capacity: LPIC_EBUFSIZE; a
+ * particle pushed to a non-finite position: LPIC_ENONFINITE) are returned by the next
+ * lpic_step whose predecessor has completed, or by the next lpic_diagnose. */
 lpic_status lpic_step(lpic_ctx *ctx, int nsteps);
 
 /* Read an observable into host memory host_out (capacity cap bytes); *written gets the
  * byte count.  Synchronises the context stream.  LPIC_EBUFSIZE if cap is too small
- * (*written then holds the size needed); LPIC_ENONFINITE if a returned scalar is NaN/Inf. */
+ * (*written then holds the size needed); LPIC_ENONFINITE if a returned scalar is NaN/Inf
+ * or a step latched a non-finite particle position. */
 lpic_status lpic_diagnose(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, size_t cap,
                           size_t *written);
 
@@ -211,7 +215,9 @@ const char *lpic_kernel_name(int k);
  * the library's device memory, present on every device that loads the library until the
  * process exits, which limits the input to (nx+1)(nr+1) <= 16,777,216 nodes (LPIC_EBUFSIZE
  * beyond).  The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  Every call rewrites
+ * device current) and keeps it for the life of the process; make that first call before
+ * any stream capture.  A cudaDeviceReset of that device invalidates the kept address: do
+ * not call this entry point on a device after resetting it.  Every call rewrites
  * the partials it uses, so nothing carries over, but all calls share the one array: calls
  * that overlap on the GPU (on different streams, or from several threads) race.
  * Returns LPIC_OK, LPIC_EINVAL (NULL pointer, sizes < 1, dr <= 0), LPIC_EBUFSIZE or

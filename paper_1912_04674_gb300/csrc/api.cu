@@ -351,6 +351,9 @@ lpic_status device_errors(lpic_ctx *c, const Desc &d) {
     if (d.err & ERR_CAPACITY)
         return c->fail(LPIC_EBUFSIZE, "particle capacity exhausted during plasma injection "
                                       "(raise particle_capacity or lower sort_every)");
+    if (d.err & ERR_NONFINITE)
+        return c->fail(LPIC_ENONFINITE, "a particle was pushed to a non-finite position "
+                                        "(non-finite momentum or field)");
     return LPIC_OK;
 }
 

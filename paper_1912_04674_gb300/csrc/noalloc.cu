@@ -79,7 +79,7 @@ __global__ void k_finish(const double *part, int nblocks, double *out) {
 extern "C" lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t nr,
                                                    double dr, double *out_dev, void *cuda_stream) {
     if (!a_dev || !out_dev || nx < 1 || nr < 1 || !(dr > 0.0)) return LPIC_EINVAL;
-    const long long n = (long long)(nx + 1) * (nr + 1);
+    const long long n = ((long long)nx + 1) * ((long long)nr + 1);
     if (n > kMaxNodes) return LPIC_EBUFSIZE;   // beyond the fixed scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LPIC_ECUDA;
@@ -97,7 +97,9 @@ extern "C" lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx
     }
     const int nblocks = (int)((n + kNodesPerBlock - 1) / kNodesPerBlock);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    (void)cudaGetLastError();   // an error left by the caller's earlier work is not ours to report
     k_partials<<<nblocks, kThreads, 0, st>>>((const double2 *)a_dev, nx, nr, dr, n, part);
+    if (cudaGetLastError() != cudaSuccess) return LPIC_ECUDA;
     k_finish<<<1, 32, 0, st>>>(part, nblocks, out_dev);
     return cudaGetLastError() == cudaSuccess ? LPIC_OK : LPIC_ECUDA;
 }

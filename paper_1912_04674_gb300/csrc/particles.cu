@@ -543,6 +543,7 @@ template <class R> struct BOut {
     R fa, fb, fra, frb;        // in-cell fractions before and after
     int ixn;                   // new lab cell (kDead when the particle leaves)
     R ox1, y1, z1;
+    bool nonfinite;            // alive with a non-finite new position (latched as ERR_NONFINITE)
 };
 
 template <class R>
@@ -603,7 +604,14 @@ __device__ __forceinline__ BOut<R> b_particle(const SimDev<R> &S, const Geo &geo
     const bool dead = irel_next < 0 || irel_next >= geo.nx || r1 >= rmax;
     o.ixn = dead ? kDead : ix + di;
     o.ox1 = ox1; o.y1 = y1; o.z1 = z1;
+    o.nonfinite = alive && !(fabs_<R>(ox1 + y1 + z1) <= (R)3.0e38);   // NaN or infinity
     return o;
+}
+
+// A non-finite pushed position (from a non-finite momentum or field) is latched in the
+// descriptor, one atomic per warp that saw one; lpic_step reports it as LPIC_ENONFINITE.
+__device__ __forceinline__ void latch_nonfinite(Desc *d, bool bad) {
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(&d->err, (int)ERR_NONFINITE);
 }
 
 // Park this warp's crossing moves in the queue (queued: same value on every lane).
@@ -656,6 +664,7 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
         const BOut<R> o = b_particle<R>(S, geo, off, shift, snext, cur.ix, cur.ox, cur.y, cur.z, cur.px,
                                         cur.py, cur.pz, cur.w);
         enqueue_cross<R>(Q, wq, queued, o, cur.w);
+        latch_nonfinite(S.d, o.nonfinite);
         const bool alive = cur.ix != kDead;
         if (DQ && alive) charge_change<R>(S, geo, off, o, cur.w);
         if (alive) {
@@ -708,6 +717,7 @@ __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S
         const BOut<float> b = b_particle<float>(S, geo, off, shift, snext, cur.ix.y, cur.ox.y, cur.y.y,
                                                 cur.z.y, m.px.y, m.py.y, m.pz.y, m.w.y);
         enqueue_cross<float>(Q, wq, queued, b, m.w.y);
+        latch_nonfinite(S.d, a.nonfinite || b.nonfinite);
         const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
         if (la && lb) {
             __stcs(reinterpret_cast<int2 *>(P.ix + k), make_int2(a.ixn, b.ixn));

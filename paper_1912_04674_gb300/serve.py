@@ -135,6 +135,8 @@ class ScanServer:
         ok = []
         for job in self.queue:
             why = validate(job.workload)
+            if why is None and (not isinstance(job.steps, (int, np.integer)) or job.steps < 0):
+                why = f"steps must be a non-negative integer (got {job.steps!r})"
             if why:
                 job.result = {"error": why}
                 job.finished = now
@@ -151,7 +153,13 @@ class ScanServer:
                            self.max_slots)
         for idx in take:
             job, (k, need) = self.queue[idx], plans[idx]
-            sim = make_simulation(job.workload, self.precision, k)
+            try:
+                sim = make_simulation(job.workload, self.precision, k)
+            except L.LpicError as e:     # this job cannot be set up: reject it alone
+                job.result = {"error": str(e)}
+                job.finished = now
+                self.rejected.append(job)
+                continue
             job.admitted = now
             self.running.append(_Running(job, sim, need))
             self.used += need

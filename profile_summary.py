@@ -1,8 +1,8 @@
 """Summarise ncu output into the short text files kept under profiles/.
 
-    python -m paper_1912_04674_gb300.profile_summary launches <launches.csv> <title> <command>
-    python -m paper_1912_04674_gb300.profile_summary capture <report.ncu-rep> <title> <command>
-    python -m paper_1912_04674_gb300.profile_summary traffic <report.ncu-rep> <precision>
+    python profile_summary.py launches <launches.csv> <title> <command>
+    python profile_summary.py capture <report.ncu-rep> <title> <command>
+    python profile_summary.py traffic <report.ncu-rep> <precision>
 
 `launches`: per kernel, the launch count, total time and share of a
 `--metrics gpu__time_duration.sum` launch list (cold-cache, serialised: compare shares).
@@ -21,7 +21,7 @@ import subprocess
 import sys
 from collections import defaultdict
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 
 KEYS = [
     ("gpu__time_duration.sum", "duration"),

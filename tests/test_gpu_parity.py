@@ -173,3 +173,22 @@ def test_async_wake_read_matches_the_synchronising_read():
     assert np.abs(buf).max() > 0
     with pytest.raises(Exception):
         g.ex_axis_async(np.zeros(3))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_non_finite_momentum_is_reported_by_the_next_call(precision):
+    """A NaN momentum (planted through the upload path; every index the kernels derive from
+    it is clamped into the grid) is pushed to a NaN position, which the position push latches
+    on the device: the next call reports LPIC_ENONFINITE instead of running on silently."""
+    from paper_1912_04674_gb300 import lpic as L
+    w = dataclasses.replace(C1, name="nan", nx=32, nr=16, sort_every=4)
+    g = gpu_from(w, precision=precision)
+    g.step(2)
+    assert g.counters()["step"] == 2
+    p = g.particles()
+    p["px"][len(p["px"]) // 2] = np.nan
+    g.upload_particles(p)
+    g.step(1)
+    with pytest.raises(L.LpicError) as e:
+        g.counters()
+    assert e.value.status == 7

@@ -39,3 +39,20 @@ def test_poisson_arrivals_are_seeded_and_have_the_rate():
     assert abs(len(t) / t[-1] / 2.0 - 1) < 0.15        # mean rate 2 jobs/s
     steps = np.array([j.steps for j in a])
     assert steps.min() >= 500 and steps.max() <= 3000
+
+
+def test_negative_step_counts_are_rejected_before_admission():
+    """A job with a negative or non-integer step count is rejected on its own; it never
+    reaches the batch (where it would stop every job in flight)."""
+    import workloads
+    srv = object.__new__(serve.ScanServer)       # host bookkeeping only: no device stream
+    srv.queue, srv.rejected, srv.running = [], [], []
+    srv.used, srv.budget, srv.max_slots, srv.max_running = 0, 0, 4, 0
+    srv.precision = "fp32"
+    w = workloads.scan_jobs(1)[0]
+    bad = [serve.Job(w, -5, 0.0, 0), serve.Job(w, 2.5, 0.0, 1)]
+    srv.queue = list(bad)
+    assert srv._admit(0.0) is False              # budget 0: nothing valid fits either
+    assert [j.job_id for j in srv.rejected] == [0, 1]
+    assert all("steps" in j.result["error"] for j in srv.rejected)
+    assert srv.queue == [] and srv.running == []
