@@ -52,6 +52,20 @@ KEYS = [
     ("smsp__sass_thread_inst_executed_op_dmul_pred_on.sum", "FP64 MUL (thread inst)"),
     ("smsp__sass_thread_inst_executed_op_dadd_pred_on.sum", "FP64 ADD (thread inst)"),
     ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active", "FP64 pipe cycles %"),
+    ("smsp__thread_inst_executed.sum", "thread instructions"),
+    ("smsp__sass_inst_executed_op_global_red.sum", "global RED instructions (warp)"),
+    ("lts__t_requests_op_red.sum", "L2 reduction requests"),
+    ("lts__t_sectors_op_red.sum", "L2 reduction sectors"),
+    ("lts__t_sectors_op_red.avg.pct_of_peak_sustained_elapsed", "L2 reduction sectors % of peak"),
+    ("lts__t_requests_op_atom.sum", "L2 atomic requests"),
+    ("lts__throughput.avg.pct_of_peak_sustained_elapsed", "L2 throughput % of peak"),
+    ("smsp__sass_inst_executed_op_shared_atom.sum", "shared atomic instructions (warp)"),
+    ("smsp__sass_inst_executed_op_shared_ld.sum", "shared load instructions (warp)"),
+    ("smsp__sass_inst_executed_op_shared_st.sum", "shared store instructions (warp)"),
+    ("l1tex__data_pipe_lsu_wavefronts_mem_shared.sum", "shared wavefronts"),
+    ("l1tex__data_pipe_lsu_wavefronts_mem_shared.avg.pct_of_peak_sustained_elapsed", "shared wavefronts % of peak"),
+    ("l1tex__data_bank_conflicts_pipe_lsu_mem_shared.sum", "shared bank conflicts"),
+    ("l1tex__throughput.avg.pct_of_peak_sustained_elapsed", "L1 throughput % of peak"),
 ]
 
 # kernels of the time step (the rest of a launch list is set-up and diagnostics)
@@ -133,6 +147,6 @@ if __name__ == "__main__":
     if mode == "launches":
         print(launches(*sys.argv[2:5]))
     elif mode == "capture":
-        print(capture(*sys.argv[2:6]))
+        print(capture(*sys.argv[2:5], *(sys.argv[5:6] or ["--set full"])))
     else:
         print(traffic(*sys.argv[2:4]))

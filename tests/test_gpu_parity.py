@@ -5,6 +5,7 @@ to 1e-10 relative in the max norm (atomic deposit order and FMA contraction are 
 differences; both are O(1e-16) per operation).  Particles are matched by id.
 """
 import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -192,3 +193,91 @@ def test_non_finite_momentum_is_reported_by_the_next_call(precision):
     with pytest.raises(L.LpicError) as e:
         g.counters()
     assert e.value.status == 7
+
+
+def test_full_c1_run_of_200_steps():
+    """Config 1 in full (paper Sec. 4 linear-wake parameters): 200 steps of the 256 x 64,
+    262,144-electron run with the moving window and the periodic sort, compared with the
+    oracle every 10 steps; the bar holds at every comparison."""
+    o = oracle_from(C1)
+    g = gpu_from(C1)
+    worst = {}
+    for _ in range(C1.steps // 10):
+        o.step(10)
+        g.step(10)
+        errs = {**field_errors(o, g), **particle_errors(o, g)}
+        worst = {k: max(worst.get(k, 0.0), v) for k, v in errs.items()}
+    assert o.step_index == g.counters()["step"] == C1.steps
+    assert g.counters()["alive"] == o.np and o.shift == g.counters()["shift"] > 150
+    bad = {k: v for k, v in worst.items() if not v <= TOL}
+    assert not bad, (bad, worst)
+
+
+def _exact_face_cells(dx, first, count):
+    """Lab cells c >= first whose face x = c dx splits back into (c, offset 0) exactly."""
+    out, c = [], first
+    while len(out) < count:
+        if math.floor((c * dx) / dx) == c and (c * dx) / dx - c == 0.0:
+            out.append(c)
+        c += 1
+    return out
+
+
+def _edge_particles(w, shift):
+    """Hand-placed electrons on the branches of the locate / push / removal logic that a
+    random lattice rarely reaches (ids 2^40 + k)."""
+    dx, dr, nx, nr = w.dx, w.dr, w.nx, w.nr
+    wt = 2e-3
+    faces = _exact_face_cells(dx, shift + 12, 3)
+    rmax = nr * dr
+    rows = [
+        # x (lab),                 y,          z,         px,   py,   pz
+        ((shift + 20.3) * dx,      0.0,        0.0,       0.0,  0.0,  0.0),   # on the axis, at rest
+        ((shift + 21.7) * dx,      0.0,        0.0,       0.2,  0.3, -0.1),   # on the axis, moving off it
+        (faces[0] * dx,            2.3,        1.1,       0.0,  0.1,  0.0),   # on an x face (offset 0)
+        (faces[1] * dx,            5 * dr,     0.0,       0.1,  0.0,  0.0),   # on an x and a radial face
+        ((shift + 17.4) * dx,      0.0,        7 * dr,    0.0,  0.0, -0.2),   # on a radial face (r/dr = 7)
+        ((shift + 25.5) * dx,      0.2,        0.05,     -0.1, -3.0, -1.0),   # crosses the axis this step
+        ((shift + 26.5) * dx,     -0.05,       0.01,      0.0,  2.0,  0.0),   # crosses the axis the other way
+        ((shift + 28.2) * dx,      rmax - 0.01, 0.0,      0.0,  1.0,  0.0),   # just below r_max, leaving
+        ((shift + 29.2) * dx,      0.0,        rmax - 0.02, 0.0, 0.0, -0.5),  # just below r_max, staying
+        (shift * dx,               3.0,        0.0,       0.0,  0.0,  0.0),   # on the back window edge
+        ((shift + 0.02) * dx,      4.0,       -1.0,      -0.5,  0.0,  0.0),   # just inside it, moving back
+        ((shift + nx - 0.02) * dx, 6.0,        0.0,       3.0,  0.0,  0.0),   # at the front, moving out
+        (faces[2] * dx,            0.0,        0.0,      -0.4,  0.0,  0.0),   # on the axis and an x face
+    ]
+    a = np.array(rows, dtype=np.float64)
+    n = len(rows)
+    return {"x": a[:, 0], "y": a[:, 1], "z": a[:, 2], "px": a[:, 3], "py": a[:, 4], "pz": a[:, 5],
+            "w": np.full(n, wt), "id": (np.uint64(1) << np.uint64(40)) + np.arange(n, dtype=np.uint64)}
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("fp32", 1e-3)])
+def test_hand_placed_edge_particles_step_by_step(precision, tol):
+    """Electrons exactly on the axis, on x and radial cell faces, crossing the axis, leaving
+    at r_max, at the back edge while the window shifts and leaving at the front, added to a
+    driven plasma: every field and particle component agrees with the oracle after each of
+    eight steps (the same particles are removed on both sides)."""
+    w = dataclasses.replace(C1, name="edges", nx=40, nr=16, a0=1.0, w0=8.0, L=5.0, n0=0.01,
+                            sort_every=3)
+    o = oracle_from(w)
+    o.step(3)
+    p = o.particles()
+    e = _edge_particles(w, o.shift)
+    both = {k: np.concatenate([p[k], e[k]]) for k in p}
+    o.set_particles(**both)
+    g = gpu_from(w, precision=precision)
+    g.upload_counters(o.step_index, o.shift)
+    for k in ("ex", "er", "bt", "a", "am"):
+        g.upload_field(k, o.field(k))
+    g.upload_particles(both)
+    for step in range(8):
+        o.step(1)
+        g.step(1)
+        fe, pe = field_errors(o, g), particle_errors(o, g)
+        bad = {k: v for k, v in {**fe, **pe}.items() if not v <= tol}
+        assert not bad, (step, bad)
+    ids = set(o.part("id").tolist())
+    gone = [k for k in range(len(e["x"])) if int(e["id"][k]) not in ids]
+    assert {7, 9, 10} <= set(gone), gone        # the r_max and back-edge removals happened
+    assert 8 not in gone and 0 not in gone
