@@ -225,6 +225,13 @@ const char *lpic_kernel_name(int k);
 lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t nr, double dr,
                                         double *out_dev, void *cuda_stream);
 
+/* Measurement helper (the paper has no counterpart): enqueues on cuda_stream one launch that
+ * keeps every SM's FP64 pipe busy with fused multiply-adds (8 independent chains of `iters`
+ * FMAs per thread, one resident wave of blocks), for timing the FP64 peak that bounds the FP64
+ * particle passes.  *flops gets the launch's FP64 operations (FMA = 2); out_dev: 2 doubles of
+ * caller-owned device memory the launch writes.  LPIC_EINVAL (iters < 1, NULL), LPIC_ECUDA. */
+lpic_status lpic_probe_fp64_fma(int32_t iters, double *out_dev, int64_t *flops, void *cuda_stream);
+
 /* Release the context (host memory only; the device buffer stays the caller's). */
 lpic_status lpic_destroy(lpic_ctx *ctx);
 

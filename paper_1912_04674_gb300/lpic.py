@@ -75,6 +75,7 @@ _SIGS = {
     "lpic_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "lpic_kernel_name": (C.c_char_p, [C.c_int]),
     "lpic_envelope_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
+    "lpic_probe_fp64_fma": (C.c_int, [C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     "lpic_bunch_scratch_bytes": (C.c_size_t, [C.c_void_p]),
     "lpic_inject_bunch": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_double, C.c_void_p, C.c_size_t]),
     "lpic_destroy": (C.c_int, [C.c_void_p]),
@@ -195,6 +196,15 @@ def lpic_envelope_stats_noalloc(a_dev_ptr: int, nx: int, nr: int, dr: float, out
                                            C.c_void_p(out_dev_ptr), C.c_void_p(stream_ptr))
     if st != LPIC_OK:
         raise LpicError(st, "lpic_envelope_stats_noalloc failed")
+
+
+def lpic_probe_fp64_fma(iters: int, out_dev_ptr: int, stream_ptr: int) -> int:
+    """Enqueue the FP64 FMA probe launch; returns its FP64 operation count."""
+    flops = C.c_int64(0)
+    st = lib().lpic_probe_fp64_fma(int(iters), C.c_void_p(out_dev_ptr), C.byref(flops), C.c_void_p(stream_ptr))
+    if st != LPIC_OK:
+        raise LpicError(st, "lpic_probe_fp64_fma failed")
+    return int(flops.value)
 
 
 def lpic_bunch_scratch_bytes(ctx) -> int:
