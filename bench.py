@@ -673,6 +673,47 @@ def large_run(steps: int = 30, horizon: int = 300, fp32_from: int = 2000):
     return out
 
 
+def slab_leg(nslab: int = 2, steps: int = 100, settle_steps: int = 300):
+    """C2 (FP32) cut into x-slabs on this one GPU (halos refreshed by lpic_slab_exchange after
+    every step) against the same workload as one window, from step `settle_steps`: the cost of
+    the decomposition's redundant halo columns and of the exchange, and the wake difference
+    (the decomposition changes only the order of atomic additions near the boundaries)."""
+    import numpy as np
+    import torch
+
+    from paper_1912_04674_gb300 import lpic as L
+    from paper_1912_04674_gb300.slabs import SlabSimulation
+    w = WORKLOAD
+    g = L.Grid(w.nx, w.nr, w.dx, w.dr, w.dt, True, w.sort_every)
+    sl = SlabSimulation(g, L.Laser(w.a0, w.w0, w.L, w.x_center, w.x_center),
+                        L.Plasma(w.n0, 0.0, w.ramp_len, w.ppc, w.seed), nslab=nslab, precision="fp32")
+    one = make_sim("fp32")
+    sl.step(settle_steps)
+    one.step(settle_steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(sl.stream)
+    sl.step(steps)
+    ev[1].record(sl.stream)
+    ev[2].record(one.stream)
+    one.step(steps)
+    ev[3].record(one.stream)
+    torch.cuda.synchronize()
+    ms_sl, ms_one = ev[0].elapsed_time(ev[1]) / steps, ev[2].elapsed_time(ev[3]) / steps
+    e1 = one.ex_axis()
+    diff = float(np.linalg.norm(sl.ex_axis() - e1) / max(np.linalg.norm(e1), 1e-300))
+    alive = one.counters()["alive"]
+    out = {"workload": w.name, "slabs": nslab, "halo": sl.halo, "from_step": settle_steps, "steps": steps,
+           "ms_per_step": ms_sl, "one_window_ms_per_step": ms_one, "value": alive / (ms_sl * 1e-3),
+           "unit": "particle-steps/s", "slab_over_one_window": ms_one / ms_sl,
+           "wake_ex_rel_l2_vs_one_window": diff,
+           "note": "all slabs on one GPU and one stream: the decomposition's overhead, not a scaling figure"}
+    sl.close()
+    one.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(max_seconds=20.0):
     from oracle.oracle import OSim
     w = WORKLOAD
@@ -726,11 +767,11 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     pk = peaks()
-    fp64pk = fp64_peak()
     result = {}
     plan = [("fp32", args.steps), ("fp64", max(3, args.steps // 8))]
     if args.precision != "both":
         plan = [p for p in plan if p[0] == args.precision]
+    fp64pk = fp64_peak() if any(p[0] == "fp64" for p in plan) else None
     for prec, k in plan:
         # clocks are sampled over the whole leg (settling, warm-up and the timed steps): the
         # timed region alone can be shorter than one sampling period
@@ -779,6 +820,7 @@ def run_ours(args):
     large = large_run() if (extras and not args.no_large) else None
     filt = filter_leg() if extras else None
     bunch = bunch_leg() if extras else None
+    slab = slab_leg() if extras else None
     scan = served_scan(args.scan_jobs) if (extras and args.scan_jobs > 0) else None
     if rank == 0 and args.precision != "both":
         print(json.dumps({"profile_run": True, "precision": args.precision, **result[args.precision]}))
@@ -803,7 +845,8 @@ def run_ours(args):
             "fp32_vs_fp64": acc,
             "grid_cell_steps_per_s": w.nx * w.nr * world / (r32["ms_per_step"] * 1e-3),
             "roofline": r32["roofline"], "kernels_ms": r32["kernels"],
-            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "filter": filt, "bunch": bunch, "batch": batch,
+            "cpu_baseline": cpu, "e2e": e2e, "large_run": large, "filter": filt, "bunch": bunch, "slabs": slab,
+            "batch": batch,
             "scan": scan, "gpu_launches": r32["gpu_launches"],
             "clocks": r32["clocks"],
         }
@@ -869,7 +912,7 @@ def main():
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
-    ap.add_argument("--only", choices=("batch", "large", "filter", "bunch"), default=None,
+    ap.add_argument("--only", choices=("batch", "large", "filter", "bunch", "slabs"), default=None,
                     help="run one leg alone and print its object (a profiling run, not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -892,6 +935,9 @@ def main():
         return
     if args.only == "bunch":
         print(json.dumps({"profile_run": True, "bunch": bunch_leg()}))
+        return
+    if args.only == "slabs":
+        print(json.dumps({"profile_run": True, "slabs": slab_leg()}))
         return
     run_ours(args)
 

@@ -73,6 +73,14 @@ typedef struct {
                                     run: 7 passes): each pass replaces Jx, Jr (and the tracked
                                     charge change) by (F_{i-1} + 2F_i + F_{i+1})/4 along x, zero
                                     outside the window; 0 = off, at most 16                   */
+    int32_t slab_x0;             /* x-slab decomposition (lpic_slab_exchange): global window
+                                    column of this grid's column 0 when the grid is one slab of
+                                    a wider window, else 0.  The context's shift counter then
+                                    reads s + slab_x0 (the lab cell of its column 0) and the
+                                    moving window still shifts when (n+1)dt >= (s+1)dx        */
+    int32_t slab_front_interior; /* 1: this slab's front column lies inside the global window,
+                                    so the moving window injects no plasma there (the exchange
+                                    fills it); 0 for the front slab or a whole window          */
 } lpic_grid_params;
 
 /* Gaussian envelope (paper Sec. 4; paraxial focused pulse, field profile exp(-xi^2/L^2)). */
@@ -224,6 +232,28 @@ const char *lpic_kernel_name(int k);
  * LPIC_ECUDA. */
 lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t nr, double dr,
                                         double *out_dev, void *cuda_stream);
+
+/* x-slab decomposition of one simulation (Sec. 3: the envelope solver parallelises with the
+ * strategies of a standard Yee scheme, i.e. sub-domains that exchange guard cells; Sec. 4 runs
+ * it on patches).  left and right are contexts of the same precision, nr, dx, dr, dt and step
+ * counter, on the same stream, holding adjacent slabs of one window: left covers global columns
+ * [x0_L, x0_L + nx_L], right starts at x0_R (their slab_x0), and they overlap by 2*halo columns
+ * around the boundary B = x0_R + halo = x0_L + nx_L - halo; left owns the cells below B and
+ * right the cells from B on.  After both have completed the same step, this call enqueues:
+ *   - E, B_theta, A^n and A^{n-1} of the owner copied into the other's halo columns (right's
+ *     nodes [B, B+halo] and cells [B, B+halo) into left; left's [B-halo, B) into right);
+ *   - left's electrons in cells >= B and right's in cells < B removed (holes until the next
+ *     sort), then right's electrons in cells [B, B+halo) appended to left and left's in
+ *     [B-halo, B) appended to right (same ids: the owner keeps its own),
+ * so that each slab computes its owned columns of the next step exactly as one whole window
+ * would: one step's phases reach at most 6 columns from a wrong boundary value (Faraday,
+ * gather, deposit, envelope, position push, current, Ampere and the window shift), so halo >= 8
+ * (>= 8 + filter_passes with the current filter) and every slab must own >= halo columns.
+ * Layout: the copies move whole columns of the persistent arrays (the sliding offsets of
+ * the two contexts are read on the device).  Errors: LPIC_EINVAL for mismatched contexts or a
+ * boundary that does not match the slab_x0/nx values; an append beyond a context's particle
+ * capacity is latched (LPIC_EBUFSIZE from that context's next call). */
+lpic_status lpic_slab_exchange(lpic_ctx *left, lpic_ctx *right, int32_t halo);
 
 /* Measurement helper (the paper has no counterpart): enqueues on cuda_stream one launch that
  * keeps every SM's FP64 pipe busy with fused multiply-adds (8 independent chains of `iters`

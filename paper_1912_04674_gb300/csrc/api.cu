@@ -53,6 +53,10 @@ lpic_status check_params(const lpic_grid_params *g, const lpic_plasma_params *p,
         msgf(msg, cap, "filter_passes=%g outside [0, %g]", g->filter_passes, kFilterMaxPasses);
         return LPIC_EINVAL;
     }
+    if (g->slab_x0 < 0 || (g->slab_front_interior != 0 && g->slab_front_interior != 1)) {
+        msgf(msg, cap, "slab_x0 must be >= 0 and slab_front_interior 0 or 1");
+        return LPIC_EINVAL;
+    }
     if (g->particle_capacity > 0 && g->sort_every < 1) {
         msgf(msg, cap, "sort_every must be >= 1 when particles are present");
         return LPIC_EINVAL;
@@ -182,13 +186,11 @@ template <class R> Kc<R> make_consts(const Phys &ph, int nr, const R *tab_dev) {
 
 std::vector<double> row_tables(const Phys &ph, int P) {
     std::vector<double> t((size_t)NTAB * P, 0.0);
-    const double dx = ph.dx, dr = ph.dr, dt = ph.dt;
+    const double dr = ph.dr;
     for (int j = 0; j < P; j++) {
-        const double vq = j == 0 ? kPi * 0.25 * dr * dr * dx : 2.0 * kPi * j * dr * dr * dx;
-        const double vchi = j == 0 ? kPi * dr * dr * dx / 3.0 : 2.0 * kPi * j * dr * dr * dx;
-        t[(size_t)T_CHI * P + j] = 1.0 / vchi;
-        t[(size_t)T_JX * P + j] = (1.0 / dt) / (vq / dx);
-        t[(size_t)T_JR * P + j] = (1.0 / dt) / (2.0 * kPi * (j + 0.5) * dr * dx);
+        t[(size_t)T_CHI * P + j] = row_ichi(ph, j);
+        t[(size_t)T_JX * P + j] = row_ijx(ph, j);
+        t[(size_t)T_JR * P + j] = row_ijr(ph, j);
         if (j > 0) {
             t[(size_t)T_ENV1R * P + j] = 1.0 / (2.0 * dr * (j * dr));
             t[(size_t)T_AMPP * P + j] = ((j + 0.5) * dr) / ((j * dr) * dr);
@@ -349,7 +351,7 @@ lpic_status push_desc(lpic_ctx *c) {
 
 lpic_status device_errors(lpic_ctx *c, const Desc &d) {
     if (d.err & ERR_CAPACITY)
-        return c->fail(LPIC_EBUFSIZE, "particle capacity exhausted during plasma injection "
+        return c->fail(LPIC_EBUFSIZE, "particle capacity exhausted (plasma injection or slab exchange) "
                                       "(raise particle_capacity or lower sort_every)");
     if (d.err & ERR_NONFINITE)
         return c->fail(LPIC_ENONFINITE, "a particle was pushed to a non-finite position "
@@ -388,8 +390,8 @@ void enqueue_step_kernels(lpic_ctx *c, const S_ &S, int npl, int inj, cudaStream
     traced(c, F_ENVELOPE, 1, st, [&] { launch_envelope(S, st); });
     if (npl > 0) traced(c, F_PASS_B, 1, st, [&] { launch_pass_b(S, npl, st); });
     if (S.ph.filter_passes > 0) traced(c, F_FILTER, 1, st, [&] { launch_filter(S, st); });
-    traced(c, F_AMPERE, 1, st, [&] { launch_ampere(S, st); });
-    traced(c, F_WINDOW, 1, st, [&] { launch_window(S, inj, st); });
+    // Ampere and the moving-window step share one launch (counted as Ampere)
+    traced(c, F_AMPERE, 1, st, [&] { launch_ampere_window(S, inj, st); });
 }
 
 int inj_upper(const lpic_ctx *c) {
@@ -401,7 +403,7 @@ bool advance_mirror(lpic_ctx *c) {
     if (window_shifts(c->ph, c->step, c->shift)) {
         c->shift += 1;
         c->off += 1;
-        if (c->ph.have_plasma)
+        if (c->ph.have_plasma && c->ph.inject)
             c->np_upper += (long long)valid_a_count(c->ph, c->shift + c->geo.nx - 1) * c->ph.ppcr *
                            c->ph.ppct * c->geo.nr;
     }
@@ -493,6 +495,8 @@ lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_preci
     c->ph.cap = (int)g->particle_capacity;
     c->ph.track_dq = g->track_continuity ? 1 : 0;
     c->ph.filter_passes = g->filter_passes;
+    c->ph.x0 = g->slab_x0;
+    c->ph.inject = g->slab_front_interior ? 0 : 1;
     c->d_desc = (Desc *)(c->buf + L.desc);
     c->key = (int *)(c->buf + L.key);
     c->count = (int *)(c->buf + L.count);
@@ -909,6 +913,35 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
     default:
         return c->fail(LPIC_EINVAL, "this kind cannot be uploaded");
     }
+}
+
+lpic_status lpic_slab_exchange(lpic_ctx *l, lpic_ctx *r, int32_t halo) {
+    if (!l || !r || l == r) return l ? l->fail(LPIC_EINVAL, "slab exchange: two distinct contexts needed") : LPIC_EINVAL;
+    auto bad = [&](const char *m) { r->fail(LPIC_EINVAL, m); return l->fail(LPIC_EINVAL, m); };
+    if (l->prec != r->prec || l->geo.nr != r->geo.nr || l->geo.P != r->geo.P || l->ph.dx != r->ph.dx ||
+        l->ph.dr != r->ph.dr || l->ph.dt != r->ph.dt || l->ph.moving_window != r->ph.moving_window)
+        return bad("slab exchange: precision, nr, dx, dr, dt and the window rule must match");
+    if (l->st != r->st) return bad("slab exchange: both contexts must use the same stream");
+    if (halo < 1 || l->geo.nx < 2 * halo || r->geo.nx < 2 * halo)
+        return bad("slab exchange: halo >= 1 and each slab at least 2*halo columns wide");
+    const long long B = (long long)r->ph.x0 + halo;
+    if (B != (long long)l->ph.x0 + l->geo.nx - halo) return bad("slab exchange: slab_x0/nx do not meet at B");
+    if (l->step != r->step || l->shift - l->ph.x0 != r->shift - r->ph.x0)
+        return bad("slab exchange: the slabs are not at the same step and window shift");
+    lpic_status s = deferred_errors(l);
+    if (s == LPIC_OK) s = deferred_errors(r);
+    if (s != LPIC_OK) return s;
+    const int B_L = (int)(B - l->ph.x0);
+    if (l->prec == LPIC_FP64) launch_slab_exchange<double>(l->sd, r->sd, B_L, halo, l->st);
+    else launch_slab_exchange<float>(l->sf, r->sf, B_L, halo, l->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return l->cuda_fail(e, "lpic_slab_exchange");
+    // appended electrons: the launch bounds and the next sort cover every slot
+    l->np_upper = l->g.particle_capacity;
+    r->np_upper = r->g.particle_capacity;
+    record_status_copy(l);
+    record_status_copy(r);
+    return LPIC_OK;
 }
 
 size_t lpic_bunch_scratch_bytes(const lpic_ctx *c) { return c ? bunch_scratch_bytes(c->geo) : 0; }

@@ -55,11 +55,12 @@ template <class R> __global__ void k_amax_waist(SimDev<R> S, double *out) {
 }
 
 // Continuity residual of the last step on interior nodes i in [1, nx-1], j in [0, nr-1]:
-// out[0] = max |dQ/dt + div I|, out[1] = max |div I|, I = J times face area.
+// out[0] = max |dQ/dt + div I|, out[1] = max |div I|, I = J times face area, i.e. the charge
+// the deposit moved through each face, over dt.
 template <class R> __global__ void k_cont(SimDev<R> S, double *out) {
     const Geo g = S.geo;
     const int off = S.d->off - S.d->last_shift;  // the window the last step deposited on
-    const double dx = S.ph.dx, dr = S.ph.dr, dt = S.ph.dt;
+    const double dt = S.ph.dt;
     // interior columns; with the current filter, also away from the `passes` columns at each
     // end, where filtering on the window only (zero outside) breaks the discrete continuity
     const int edge = 1 + S.ph.filter_passes;
@@ -68,11 +69,10 @@ template <class R> __global__ void k_cont(SimDev<R> S, double *out) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = edge + (int)(t / g.nr), j = (int)(t % g.nr);
-        const double ax = j == 0 ? kPi * 0.25 * dr * dr : 2.0 * kPi * j * dr * dr;
-        const double ixp = S.f.jxu[g.at(off, i, j)] * ax, ixm = S.f.jxu[g.at(off, i - 1, j)] * ax;
-        const double irp = S.f.jru[g.at(off, i, j)] * 2.0 * kPi * (j + 0.5) * dr * dx;
-        const double irm = j == 0 ? 0.0 : S.f.jru[g.at(off, i, j - 1)] * 2.0 * kPi * (j - 0.5) * dr * dx;
-        const double div = (ixp - ixm) + (irp - irm);
+        const double ixp = S.f.jxu[g.at(off, i, j)], ixm = S.f.jxu[g.at(off, i - 1, j)];
+        const double irp = S.f.jru[g.at(off, i, j)];
+        const double irm = j == 0 ? 0.0 : S.f.jru[g.at(off, i, j - 1)];
+        const double div = ((ixp - ixm) + (irp - irm)) / dt;
         const double res = S.f.dqu[g.at(off, i, j)] / dt + div;
         rmax = fmax(rmax, fabs(res));
         dmax = fmax(dmax, fabs(div));
@@ -214,9 +214,9 @@ template <class R> __global__ void k_dump_field(SimDev<R> S, int kind, int c0, i
             st[2 * t + 1] = a.y;
             break;
         }
-        case 15: st[t] = S.f.chi[id]; break;
-        case 16: st[t] = S.f.jxu[id]; break;
-        case 17: st[t] = S.f.jru[id]; break;
+        case 15: st[t] = S.f.chi[id] * row_ichi(S.ph, j); break;
+        case 16: st[t] = S.f.jxu[id] * row_ijx(S.ph, j); break;
+        case 17: st[t] = S.f.jru[id] * row_ijr(S.ph, j); break;
         case 18: st[t] = S.f.dqu[id]; break;
         }
     }

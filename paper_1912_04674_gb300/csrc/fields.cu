@@ -6,6 +6,7 @@
 // row j = 0 of the envelope and of the Ex update is computed in FP64 (the 1/r and 4/dr
 // axis terms); everything else in the working precision R.
 #include "lpic_internal.cuh"
+#include "window.cuh"
 
 namespace lpic {
 
@@ -25,9 +26,17 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
     const int off = S.d->off;
     const int j = bx * BX + threadIdx.x;
     const int i = by * BY + (int)threadIdx.y - kG;
+    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) S.d->off_step = off;
     if (j >= g.P || i > g.nx + kG) return;
     const long long id = g.at(off, i, j);
     const R dt = S.k.dt, idx_ = S.k.idx, idr = S.k.idr;
+    if (i == -1) {
+        // the guard column left of the window: the Ampere launch that folds in the window step
+        // leaves E and B_theta there (its old column 0) for this kernel to zero
+        S.f.ex[id] = (R)0;
+        S.f.er[id] = (R)0;
+        S.f.bt[id] = (R)0;
+    }
 
     R btn_here = (R)0;
     if (i >= 0 && i < g.nx && j < g.nr) {
@@ -155,8 +164,8 @@ __device__ __forceinline__ void envelope_tile(const SimDev<R> &S, int bx, int by
     const Kc<R> &K = S.k;
     R nre, nim;
     envelope_node<R>(c, A[g.at(off, i + 1, j)], A[g.at(off, i - 1, j)], A[id + 1], A[id - 1],
-                     S.f.a[ab ^ 1][id], from_acc<R>(S.f.chi[id]), false, K.idx2, K.idr2,
-                     K.tab[T_ENV1R * g.P + j], K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
+                     S.f.a[ab ^ 1][id], from_acc<R>(S.f.chi[id]) * K.tab[T_CHI * g.P + j], false, K.idx2,
+                     K.idr2, K.tab[T_ENV1R * g.P + j], K.hidx, K.dt, K.dt2, K.envp, K.envpt, nre, nim);
     envelope_store<R>(S, id, ab, c, nre, nim);
 }
 
@@ -175,16 +184,15 @@ template <class R> __device__ __forceinline__ void envelope_axis_node(const SimD
     const Kc<R> &K = S.k;
     double dre, dim;
     envelope_node<double>(c, A[g.at(off, i + 1, 0)], A[g.at(off, i - 1, 0)], A[id + 1], c,
-                          S.f.a[ab ^ 1][id], S.f.chi[id], true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
+                          S.f.a[ab ^ 1][id], S.f.chi[id] * row_ichi(S.ph, 0), true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
                           K.d_dt, K.d_dt2, K.d_envp, K.d_envpt, dre, dim);
     envelope_store<R>(S, id, ab, c, (R)dre, (R)dim);
 }
 
 // Ampere (Eq. MaxwellEqsCylindrical, second and third equations): Er on (i, j+1/2) with
 // Er = 0 on the x ends; Ex on (i+1/2, j) with the axis row 4 B_{1/2}/dr and Ex = 0 at r_max.
-template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &S, int bx, int by) {
+template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &S, int off, int bx, int by) {
     const Geo g = S.geo;
-    const int off = S.d->off;
     const int j = bx * BX + threadIdx.x;
     const int i = by * BY + threadIdx.y;
     if (j > g.nr || i > g.nx) return;
@@ -195,7 +203,7 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.er[id] = (R)0;
         } else {
             R dbdx = (S.f.bt[id] - S.f.bt[g.at(off, i - 1, j)]) * S.k.idx;
-            S.f.er[id] += dt * (-dbdx - from_acc<R>(S.f.jru[id]));
+            S.f.er[id] += dt * (-dbdx - from_acc<R>(S.f.jru[id]) * S.k.tab[T_JR * g.P + j]);
         }
     }
     if (i < g.nx) {
@@ -203,15 +211,35 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.ex[id] = (R)0;
         } else if (j == 0) {  // axis row in FP64
             double curl = S.k.d_4idr * (double)S.f.bt[id];
-            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jxu[id]));
+            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jxu[id] * row_ijx(S.ph, 0)));
         } else {
             R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
-            S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jxu[id]));
+            S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jxu[id]) * S.k.tab[T_JX * g.P + j]);
         }
     }
 }
 
-template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, blockIdx.x, blockIdx.y); }
+template <class R> __global__ void k_ampere(SimDev<R> S) { ampere_tile<R>(S, S.d->off, blockIdx.x, blockIdx.y); }
+
+// Ampere with the step's moving-window work folded into the same launch: blocks [0, gw) zero
+// the new guard columns and inject the plasma of the new front column (first, so that their
+// latency-bound work starts with the launch), and the last of them advances the counters; the
+// other blocks are the Ampere tiles, one per block.  Ampere addresses the grid through the
+// offset the step began with (off_step), so it does not matter when the window blocks move
+// `off`; E and B_theta of the old column 0, which Ampere updates and which becomes the guard
+// column -1, are zeroed by the next step's prepass.  One launch instead of two, and no Ampere
+// block waits for or counts anything.
+template <class R> __global__ void __launch_bounds__(BX * BY) k_ampere_window(SimDev<R> S, int tiles_x, int gw) {
+    const int b = blockIdx.x;
+    if (b < gw) {
+        __shared__ ColumnPlan<R> cp;
+        window_fill<R>(S, b * (BX * BY) + threadIdx.y * BX + threadIdx.x, gw * (BX * BY), true, cp);
+        window_done<R>(S, (unsigned)gw);
+    } else {
+        const int t = b - gw;
+        ampere_tile<R>(S, S.d->off_step, t % tiles_x, t / tiles_x);
+    }
+}
 
 // Binomial current filter (Sec. 4: an uncompensated binomial filter of 7 passes against
 // numerical Cherenkov radiation): each pass replaces F_i by (F_{i-1} + 2 F_i + F_{i+1})/4 along x,
@@ -318,7 +346,7 @@ template <class R>
 __global__ void __launch_bounds__(BX * BY) k_ampere_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int4 it = items[w];
-        ampere_tile<R>(pk.v[it.x], it.y, it.z);
+        ampere_tile<R>(pk.v[it.x], pk.v[it.x].d->off, it.y, it.z);
     }
 }
 template <class R>
@@ -392,6 +420,13 @@ template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st) {
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st) {
     k_ampere<R><<<grid2(S.geo.nr + 1, S.geo.nx + 1), dim3(BX, BY), 0, st>>>(S);
 }
+template <class R> void launch_ampere_window(const SimDev<R> &S, int inj_upper, cudaStream_t st) {
+    const dim3 t = grid2(S.geo.nr + 1, S.geo.nx + 1);
+    int work = (2 * kG + 1) * S.geo.P;
+    if (inj_upper > work) work = inj_upper;
+    const int gw = (work + BX * BY - 1) / (BX * BY);
+    k_ampere_window<R><<<(int)(t.x * t.y) + gw, dim3(BX, BY), 0, st>>>(S, (int)t.x, gw);
+}
 template <class R> void launch_filter(const SimDev<R> &S, cudaStream_t st) {
     int tx, ty;
     grid_tiles(S.geo, 3, tx, ty);
@@ -450,6 +485,7 @@ void launch_grid_multi(int phase, const SimPack<R> &pk, const int4 *items, int n
     template void launch_prepass<R>(const SimDev<R> &, cudaStream_t);                        \
     template void launch_envelope<R>(const SimDev<R> &, cudaStream_t);                       \
     template void launch_ampere<R>(const SimDev<R> &, cudaStream_t);                         \
+    template void launch_ampere_window<R>(const SimDev<R> &, int, cudaStream_t);             \
     template void launch_filter<R>(const SimDev<R> &, cudaStream_t);                         \
     template void launch_init_envelope<R>(const SimDev<R> &, double, double, double, double, \
                                           double, cudaStream_t);                             \

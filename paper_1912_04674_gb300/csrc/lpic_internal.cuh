@@ -35,7 +35,9 @@ struct Desc {
     int last_shift;    // 1 if the last step ended with a window shift (its deposits sit one
                        // physical column before the current window)
     unsigned done;     // blocks of the window kernel finished this step (last one advances)
-    int pad[4];
+    int off_step;      // `off` as the step began (copied by the prepass): Ampere reads it while
+                       // the window step, in the same launch, may already have advanced `off`
+    int pad[3];
 };
 static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
 
@@ -69,7 +71,9 @@ template <class R> struct Fields {
     // element of row -1 (the spare last row of the previous column) is (-F(i, 0), F(i, 0)),
     // the odd mirror of Er and Btheta across the axis
     typename Cplx<R>::t *exq, *erq, *btq;
-    double *chi, *jx, *jr, *dq;      // per step FP64 accumulators (deposit targets)
+    double *chi, *jx, *jr, *dq;      // per step FP64 accumulators (deposit targets), before
+                                     // their row factors (RowTab): chi sum w S/gamma, Jx and
+                                     // Jr the charge through each face in the step
     // the current (and charge change) the fields see: the deposit targets, or, with the
     // binomial filter on, separate arrays the filter writes from them
     double *jxu, *jru, *dqu;
@@ -91,11 +95,16 @@ struct Phys {
     int cap;
     int track_dq;
     int filter_passes;   // binomial current filter passes after the deposit (0: off)
+    int x0;              // x-slab: global window column of column 0 (0 for a whole window)
+    int inject;          // 1: the moving window injects plasma at the front column
     // host-computed reciprocals for the lattice generator
     double inv_ramp, inv_ppcx, inv_ppcr, inv_ppct, wfac;  // wfac = 2 pi dr dx / ppc
 };
 
 // Per-row tables (device, P entries each, working precision), filled once at set-up.
+// The particle passes deposit per-row-free sums (chi: sum w S / gamma; Jx, Jr: the charge
+// moved through each face in the step), and the grid kernels that read them apply these row
+// factors (one multiply per node instead of one per particle and node).
 enum RowTab : int {
     T_CHI = 0,   // 1 / V_chi(j)
     T_JX,        // (1/dt) / (V_j / dx): current from a charge flux through an x face
@@ -105,6 +114,21 @@ enum RowTab : int {
     T_AMPM,      // r_{j-1/2} / (r_j dr), j >= 1
     NTAB
 };
+
+// The row factors in FP64 (the host tables and the FP64 axis rows use these; dumps too).
+// Volumes (G7): V_j = 2 pi j dr^2 dx (j >= 1), charge and current V_0 = pi (dr/2)^2 dx,
+// susceptibility V_chi,0 = pi dr^2 dx / 3.
+__host__ __device__ __forceinline__ double row_ichi(const Phys &ph, int j) {
+    const double vchi = j == 0 ? kPi * ph.dr * ph.dr * ph.dx / 3.0 : 2.0 * kPi * j * ph.dr * ph.dr * ph.dx;
+    return 1.0 / vchi;
+}
+__host__ __device__ __forceinline__ double row_ijx(const Phys &ph, int j) {
+    const double vq = j == 0 ? kPi * 0.25 * ph.dr * ph.dr * ph.dx : 2.0 * kPi * j * ph.dr * ph.dr * ph.dx;
+    return (1.0 / ph.dt) / (vq / ph.dx);
+}
+__host__ __device__ __forceinline__ double row_ijr(const Phys &ph, int j) {
+    return (1.0 / ph.dt) / (2.0 * kPi * (j + 0.5) * ph.dr * ph.dx);
+}
 
 // Constants of one simulation, computed on the host (FP64 is a slow pipe on this part,
 // so no kernel derives them per thread).
@@ -205,10 +229,11 @@ __host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long 
     return z ^ (z >> 31);
 }
 
-// Does the window shift after step n (window speed c)?  Same double arithmetic on host
-// and device.
+// Does the window shift after step n (window speed c)?  s is the context's shift counter,
+// the lab cell of its column 0: the global shift count plus the slab offset x0.  Same double
+// arithmetic on host and device.
 __host__ __device__ __forceinline__ bool window_shifts(const Phys &ph, long long n, long long s) {
-    return ph.moving_window && (double)(n + 1) * ph.dt >= (double)(s + 1) * ph.dx;
+    return ph.moving_window && (double)(n + 1) * ph.dt >= (double)(s - ph.x0 + 1) * ph.dx;
 }
 
 // Plasma lattice of lab column c (regular ppc_x x ppc_r x ppc_theta per cell, weight
@@ -284,15 +309,22 @@ template <class R> void launch_pass_a(const SimDev<R> &S, int np_upper, cudaStre
 template <class R> void launch_envelope(const SimDev<R> &S, cudaStream_t st);
 template <class R> void launch_pass_b(const SimDev<R> &S, int np_upper, cudaStream_t st);
 template <class R> void launch_ampere(const SimDev<R> &S, cudaStream_t st);
+// Ampere and the end-of-step window (guard zeroing, injection, counters) in one launch
+template <class R> void launch_ampere_window(const SimDev<R> &S, int inj_upper, cudaStream_t st);
 template <class R> void launch_filter(const SimDev<R> &S, cudaStream_t st);
 constexpr int kFilterMaxPasses = 16;
-template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st);
 
 template <class R> void launch_init_envelope(const SimDev<R> &S, double a0, double w0, double L,
                                             double xc, double xf, cudaStream_t st);
 template <class R> void launch_load_columns(const SimDev<R> &S, const int *d_colbase, int ncols,
                                             int total, cudaStream_t st);
 template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStream_t st);
+
+// ---- x-slab exchange (slab.cu): halo columns of the persistent arrays from the owner, then
+// the electrons: remove those outside [lo, hi) (local cells) from each side and append the
+// other side's electrons in its halo cells.
+template <class R>
+void launch_slab_exchange(const SimDev<R> &L, const SimDev<R> &Rt, int B_L, int halo, cudaStream_t st);
 
 // ---- injected bunch: its charge from particle slots [k0, k0 + n), the discrete Gauss-law solve
 // (preconditioned CG to relative residual tol, at most max_iter iterations) and the addition of
@@ -334,7 +366,7 @@ void launch_sort_multi(const SimPack<R> &pk, const int *due, const int4 *blocks,
 constexpr int kSortLaunchesMulti = 7;
 __host__ __device__ inline int sort_blocks(const Geo &g) { return (g.nx * g.nr + 1 + 4095) / 4096; }
 constexpr int kWindowThreads = 64;
-int window_parts(const Geo &g, int work);   // blocks of the single-simulation window launch
+int window_parts(const Geo &g, int work);   // parts of one simulation's window step in the fused batch launch
 
 // exclusive scan of n ints in place (n <= 4096 * 4096); blocksum: ceil(n/4096)+1 ints
 void scan_exclusive(int *data, int n, int *blocksum, cudaStream_t st);

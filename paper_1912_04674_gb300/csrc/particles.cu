@@ -216,7 +216,6 @@ template <class R, bool PAIRED = false>
 __device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo, int off, long long shift,
                                               int ix, R ox, R y, R z, R px, R py, R pz, R w) {
     const R hdt = S.k.hdt, idr = S.k.idr;
-    const R *__restrict__ tchi = S.k.tab + T_CHI * geo.P;
     const R q = (R)-1;
     const bool alive = ix != kDead;
     const int irel = (int)((long long)ix - shift);
@@ -256,13 +255,12 @@ __device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo
     const R sz = pz + hdt * (q * Ez - Gz * i2g0);
     const R rgt = rsqrt_<R>((R)1 + sx * sx + sy * sy + sz * sz + phg);   // 1/gt
 
-    // susceptibility: w S/(gt V) on the four primal nodes (q^2/m = 1), 1/V per row
+    // susceptibility: w S/gt on the four primal nodes (q^2/m = 1); the envelope applies 1/V_chi
+    // per row
     AOut<R> o;
-    const R i0 = tchi[L.jp], i1 = tchi[L.jp + 1];
     const R base_w = alive ? w * rgt : (R)0;
-    const R c0 = base_w * i0, c1 = base_w * i1;
-    o.v[0] = c0 * w00; o.v[1] = c0 * w10; o.v[2] = c1 * w01; o.v[3] = c1 * w11;
-    o.bnd = c0 > c1 ? c0 : c1;
+    o.v[0] = base_w * w00; o.v[1] = base_w * w10; o.v[2] = base_w * w01; o.v[3] = base_w * w11;
+    o.bnd = base_w;
     o.key = alive ? (unsigned)b : kNoKey;
     o.b = b;
 
@@ -467,7 +465,8 @@ template <class R> __device__ __forceinline__ void shape3(int i0, R f, int base,
 }
 
 // Cell-crossing particles of one warp, parked until the warp can process 32 of them at once.
-constexpr int QW = 64;                 // entries per warp (at most 32 join per enqueue; drained at 32)
+constexpr int QW = 96;                 // entries per warp: drained at 32 once per iteration, in
+                                       // which at most 64 join (two particles per lane)
 constexpr int NWARP = TPB_B / 32;
 template <class R> struct CrossQueue {
     int ia[NWARP][QW], ja[NWARP][QW], di[NWARP][QW], dj[NWARP][QW];
@@ -479,8 +478,6 @@ template <class R>
 __device__ __forceinline__ void deposit_general(const SimDev<R> &S, int off, int ia, int ib,
                                                 R fa, R fb, int ja, int jb, R fra, R frb, R w) {
     const Geo &geo = S.geo;
-    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
-    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
     const int imin = min(ia, ib), jmin = min(ja, jb);
     R s0x[3], s1x[3], s0r[3], s1r[3], dsx[3], dsr[3];
     shape3<R>(ia, fa, imin, s0x);
@@ -496,7 +493,7 @@ __device__ __forceinline__ void deposit_general(const SimDev<R> &S, int off, int
 #pragma unroll
         for (int cc = 0; cc < 2; cc++) {
             acc += dsx[cc] * (s0r[l] + (R)0.5 * dsr[l]);
-            atom_add(S.f.jx + bb + cc * geo.P + l, w * acc * tjx[jmin + l]);
+            atom_add(S.f.jx + bb + cc * geo.P + l, w * acc);
         }
     }
 #pragma unroll
@@ -505,7 +502,7 @@ __device__ __forceinline__ void deposit_general(const SimDev<R> &S, int off, int
 #pragma unroll
         for (int l = 0; l < 2; l++) {
             acc += dsr[l] * (s0x[cc] + (R)0.5 * dsx[cc]);
-            atom_add(S.f.jr + bb + cc * geo.P + l, w * acc * tjr[jmin + l]);
+            atom_add(S.f.jr + bb + cc * geo.P + l, w * acc);
         }
     }
 }
@@ -524,7 +521,9 @@ __device__ __forceinline__ void drain_queue(const SimDev<R> &S, int off, CrossQu
 // charge-conserving current in the (x, r) index plane (Esirkepov decomposition):
 //   Wx = DSx (S0r + DSr/2), Wr = DSr (S0x + DSx/2),
 //   Jx(i+1/2,j) = (-q w/dt) sum_{k<=i} Wx(k,j) / (V_j/dx),
-//   Jr(i,j+1/2) = (-q w/dt) sum_{l<=j} Wr(i,l) / (2 pi r_{j+1/2} dx).
+//   Jr(i,j+1/2) = (-q w/dt) sum_{l<=j} Wr(i,l) / (2 pi r_{j+1/2} dx);
+// the deposit is the charge -q w sum Wx (sum Wr) through each face, and Ampere applies the
+// per-row factors 1/(dt V_j/dx) and 1/(dt 2 pi r_{j+1/2} dx).
 // A particle that stays in its cell has only four non-zero terms,
 //   Jx(i+1/2, j)   ~ -w dx_ (1 - rbar),  Jx(i+1/2, j+1) ~ -w dx_ rbar,
 //   Jr(i, j+1/2)   ~ -w dr_ (1 - xbar),  Jr(i+1, j+1/2) ~ -w dr_ xbar,
@@ -537,7 +536,8 @@ __device__ __forceinline__ void drain_queue(const SimDev<R> &S, int off, CrossQu
 template <class R> struct BOut {
     unsigned key;              // b for a particle that stays in its cell, else kNoKey
     int b;                     // its cell base (window-relative node index)
-    R v[4], bnd[2];            // Jx(i+1/2, j), Jx(i+1/2, j+1), Jr(i, j+1/2), Jr(i+1, j+1/2)
+    R v[4], bnd[2];            // charge through the faces of Jx(i+1/2, j), Jx(i+1/2, j+1),
+                               // Jr(i, j+1/2), Jr(i+1, j+1/2)
     bool cross;                // alive and leaving its cell: the general deposit
     int ia, ja, di, dj;        // the move, in cells
     R fa, fb, fra, frb;        // in-cell fractions before and after
@@ -551,8 +551,6 @@ __device__ __forceinline__ BOut<R> b_particle(const SimDev<R> &S, const Geo &geo
                                               int snext, int ix, R ox, R y, R z, R px, R py, R pz, R w) {
     const R dt = S.k.dt, idr = S.k.idr, dtdx = S.k.dtdx;
     const R rmax = S.k.rmax;
-    const R *__restrict__ tjx = S.k.tab + T_JX * geo.P;
-    const R *__restrict__ tjr = S.k.tab + T_JR * geo.P;
     const bool alive = ix != kDead;
     const int irel = (int)((long long)ix - shift);
     const R r0 = sqrt_<R>(y * y + z * z);
@@ -586,15 +584,15 @@ __device__ __forceinline__ BOut<R> b_particle(const SimDev<R> &S, const Geo &geo
     const R xbar = (R)0.5 * (ox + ox1), rbar = (R)0.5 * (fra + frb);
     const bool fast = alive && stays;
     const R bx = fast ? w * ddx : (R)0, br = fast ? w * ddr : (R)0;
-    // row factors 1/(dt A_j) of the two x faces and 1/(dt 2 pi r_{j+1/2} dx) of the r face
-    const R fx0 = tjx[ja], fx1 = tjx[ja + 1], fr = tjr[ja];
-    const R cx = -bx, cr = -br * fr;
-    o.v[0] = cx * ((R)1 - rbar) * fx0;
-    o.v[1] = cx * rbar * fx1;
+    // the charge moved through the two x faces and the r face (Ampere applies the row factors
+    // 1/(dt A_j) and 1/(dt 2 pi r_{j+1/2} dx))
+    const R cx = -bx, cr = -br;
+    o.v[0] = cx * ((R)1 - rbar);
+    o.v[1] = cx * rbar;
     o.v[2] = cr * ((R)1 - xbar);
     o.v[3] = cr * xbar;
-    o.bnd[0] = fabs_<R>(bx) * (fx0 > fx1 ? fx0 : fx1);
-    o.bnd[1] = fabs_<R>(cr);
+    o.bnd[0] = fabs_<R>(bx);
+    o.bnd[1] = fabs_<R>(br);
     o.b = geo.at(off, ia, ja);
     o.key = fast ? (unsigned)o.b : kNoKey;
     o.cross = alive && !stays;
@@ -687,9 +685,9 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
 }
 
 // FP32: two neighbouring particles per thread, as in pass A; the crossing moves of each half
-// join the queue in turn (draining at 32 after each keeps it within QW), the first before the
-// second is computed, which frees its registers (measured 11 % faster than computing both
-// first, with spills gone).
+// join the queue in turn, the first before the second is computed, which frees its registers
+// (measured 11 % faster than computing both first, with spills gone); the queue is drained at
+// one place per iteration (one inlined copy of the general deposit, not two).
 template <>
 __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S, int vb, int nvb, int csize) {
     __shared__ CrossQueue<float> Q;
@@ -710,10 +708,6 @@ __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S
         const BOut<float> a = b_particle<float>(S, geo, off, shift, snext, cur.ix.x, cur.ox.x, cur.y.x,
                                                 cur.z.x, m.px.x, m.py.x, m.pz.x, m.w.x);
         enqueue_cross<float>(Q, wq, queued, a, m.w.x);
-        if (queued >= 32) {
-            drain_queue<float>(S, off, Q, wq, queued);
-            queued = 0;
-        }
         const BOut<float> b = b_particle<float>(S, geo, off, shift, snext, cur.ix.y, cur.ox.y, cur.y.y,
                                                 cur.z.y, m.px.y, m.py.y, m.pz.y, m.w.y);
         enqueue_cross<float>(Q, wq, queued, b, m.w.y);

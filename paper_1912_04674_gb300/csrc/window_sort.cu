@@ -1,6 +1,7 @@
 // Moving window (shift bookkeeping, guard zeroing, plasma injection at the front), step
 // counter advance, and the periodic counting sort of particles by cell.
 #include "lpic_internal.cuh"
+#include "window.cuh"
 
 namespace lpic {
 
@@ -8,72 +9,12 @@ namespace {
 
 constexpr int TPB = 256;
 
-// End of step n.  If the window shifts (paper Sec. 4 runs use a window moving at c), the live
-// window slides one physical column, the guard columns of the persistent arrays on both
-// sides of the new window are zeroed (the new front column of A and Er is among them), and
-// the new last cell column is filled with the plasma lattice at slots [np, np+count).  The
-// last block to finish then advances the counters (no block waits for another).
+// One part of the window step of one simulation (window.cuh): parts of kWindowThreads threads.
 template <class R> __device__ __forceinline__ void window_body(const SimDev<R> &S, int part, int nparts) {
-    const long long n = S.d->step, s = S.d->shift;
-    const bool shifting = window_shifts(S.ph, n, s);
-    const Geo g = S.geo;
-    const int tid = part * blockDim.x + threadIdx.x, nth = nparts * blockDim.x;
-    const int np = S.d->np;
-    const long long c = s + g.nx;  // lab column of the new last cell column
-    int count = 0;
-    bool inject = false;
-    if (shifting) {
-        const int noff = S.d->off + 1;
-        // columns i in [-kG, -1] and [nx, nx+kG] of the new window
-        const int ncz = 2 * kG + 1;
-        for (int t = tid; t < ncz * g.P; t += nth) {
-            const int cc = t / g.P, j = t - cc * g.P;
-            const int i = cc < kG ? cc - kG : g.nx + (cc - kG);
-            const long long id = g.at(noff, i, j);
-            S.f.ex[id] = (R)0;
-            S.f.er[id] = (R)0;
-            S.f.bt[id] = (R)0;
-            typename Cplx<R>::t zc;
-            zc.x = (R)0;
-            zc.y = (R)0;
-            S.f.a[0][id] = zc;
-            S.f.a[1][id] = zc;
-        }
-        if (S.ph.have_plasma) {
-            // the column's lattice slices and densities, once per block
-            __shared__ ColumnPlan<R> cp;
-            if (threadIdx.x == 0) column_plan<R>(S.ph, c, cp);
-            __syncthreads();
-            count = column_particles<R>(S.ph, cp, g.nr);
-            inject = np + count <= S.ph.cap;
-            if (inject)
-                for (int t = tid; t < count; t += nth) lattice_emit<R>(S, cp, c, t, np + t);
-        }
-    }
-    // last block: advance the counters once every block is done with them
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&S.d->done, 1u);
-        if (prev == (unsigned)nparts - 1) {
-            Desc *d = S.d;
-            d->done = 0;
-            d->last_shift = shifting ? 1 : 0;
-            if (shifting) {
-                if (S.ph.have_plasma) {
-                    if (inject) d->np = np + count;
-                    else d->err |= ERR_CAPACITY;
-                }
-                d->shift = s + 1;
-                d->off += 1;
-            }
-            d->step = n + 1;
-            d->abuf ^= 1;
-        }
-    }
+    __shared__ ColumnPlan<R> cp;
+    window_fill<R>(S, part * blockDim.x + threadIdx.x, nparts * blockDim.x, false, cp);
+    window_done<R>(S, (unsigned)nparts);
 }
-
-template <class R> __global__ void k_window(SimDev<R> S) { window_body<R>(S, blockIdx.x, gridDim.x); }
 
 // Fused form over a batch: items {simulation, part, parts of that simulation}.
 template <class R> __global__ void k_window_multi(const __grid_constant__ SimPack<R> pk, const int4 *items, int n) {
@@ -329,13 +270,6 @@ int window_parts(const Geo &g, int work) {
     return blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks);
 }
 
-template <class R> void launch_window(const SimDev<R> &S, int inj_upper, cudaStream_t st) {
-    int work = (2 * kG + 1) * S.geo.P;
-    if (inj_upper > work) work = inj_upper;
-    // small blocks: the per-particle lattice arithmetic is FP64 and should spread over SMs
-    k_window<R><<<window_parts(S.geo, work), kWindowThreads, 0, st>>>(S);
-}
-
 template <class R> void launch_window_multi(const SimPack<R> &pk, const int4 *items, int n, cudaStream_t st) {
     if (n > 0) k_window_multi<R><<<n < 152 * 8 ? n : 152 * 8, kWindowThreads, 0, st>>>(pk, items, n);
 }
@@ -378,7 +312,6 @@ void launch_sort_multi(const SimPack<R> &pk, const int *due, const int4 *blocks,
 #define INST(R)                                                                          \
     template void launch_sort_multi<R>(const SimPack<R> &, const int *, const int4 *, int, \
                                        const int4 *, int, const int4 *, int, cudaStream_t); \
-    template void launch_window<R>(const SimDev<R> &, int, cudaStream_t);                \
     template void launch_window_multi<R>(const SimPack<R> &, const int4 *, int, cudaStream_t); \
     template void launch_sort<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t);
 INST(double)

@@ -42,7 +42,8 @@ class lpic_grid_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("nr", C.c_int32), ("dx", C.c_double), ("dr", C.c_double),
                 ("dt", C.c_double), ("moving_window", C.c_int32), ("sort_every", C.c_int32),
                 ("particle_capacity", C.c_int64), ("track_continuity", C.c_int32),
-                ("accel_px_min", C.c_double), ("filter_passes", C.c_int32)]
+                ("accel_px_min", C.c_double), ("filter_passes", C.c_int32), ("slab_x0", C.c_int32),
+                ("slab_front_interior", C.c_int32)]
 
 
 class lpic_laser_params(C.Structure):
@@ -75,6 +76,7 @@ _SIGS = {
     "lpic_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
     "lpic_kernel_name": (C.c_char_p, [C.c_int]),
     "lpic_envelope_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
+    "lpic_slab_exchange": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "lpic_probe_fp64_fma": (C.c_int, [C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     "lpic_bunch_scratch_bytes": (C.c_size_t, [C.c_void_p]),
     "lpic_inject_bunch": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_double, C.c_void_p, C.c_size_t]),
@@ -196,6 +198,10 @@ def lpic_envelope_stats_noalloc(a_dev_ptr: int, nx: int, nr: int, dr: float, out
                                            C.c_void_p(out_dev_ptr), C.c_void_p(stream_ptr))
     if st != LPIC_OK:
         raise LpicError(st, "lpic_envelope_stats_noalloc failed")
+
+
+def lpic_slab_exchange(left, right, halo: int):
+    _check(lib().lpic_slab_exchange(left, right, int(halo)), left)
 
 
 def lpic_probe_fp64_fma(iters: int, out_dev_ptr: int, stream_ptr: int) -> int:
@@ -323,6 +329,8 @@ class Grid:
     track_continuity: bool = False
     accel_px_min: float = 0.0
     filter_passes: int = 0
+    slab_x0: int = 0                  # x-slab: global window column of column 0
+    slab_front_interior: bool = False  # x-slab whose front column is inside the window
 
 
 @dataclass
@@ -345,7 +353,8 @@ class Plasma:
 
 def grid_struct(g: Grid, plasma: Plasma | None = None, capacity: int | None = None) -> lpic_grid_params:
     s = lpic_grid_params(g.nx, g.nr, g.dx, g.dr, g.dt, int(g.moving_window), int(g.sort_every), 0,
-                         int(g.track_continuity), float(g.accel_px_min), int(g.filter_passes))
+                         int(g.track_continuity), float(g.accel_px_min), int(g.filter_passes),
+                         int(g.slab_x0), int(bool(g.slab_front_interior)))
     if capacity is not None:
         s.particle_capacity = int(capacity)
     elif plasma is not None:

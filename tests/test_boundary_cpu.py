@@ -43,13 +43,13 @@ def test_struct_layout_matches_c(L, tmp_path):
     src.write_text('#include "lpic.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
                    'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lpic_grid_params), sizeof(lpic_laser_params),'
                    'sizeof(lpic_plasma_params), offsetof(lpic_grid_params, particle_capacity),'
-                   'offsetof(lpic_plasma_params, seed), offsetof(lpic_grid_params, filter_passes));return 0;}\n')
+                   'offsetof(lpic_plasma_params, seed), offsetof(lpic_grid_params, slab_front_interior));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(L.lpic_grid_params), C.sizeof(L.lpic_laser_params),
                    C.sizeof(L.lpic_plasma_params), L.lpic_grid_params.particle_capacity.offset,
-                   L.lpic_plasma_params.seed.offset, L.lpic_grid_params.filter_passes.offset]
+                   L.lpic_plasma_params.seed.offset, L.lpic_grid_params.slab_front_interior.offset]
 
 
 def paper_cases():

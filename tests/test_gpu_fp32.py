@@ -100,3 +100,33 @@ def test_fp32_ragged_grids_and_odd_particle_counts(nx, nr, ppc):
     assert o.shift >= 9
     if ppc == (3, 1, 1):
         assert odd
+
+
+def test_fp32_difference_grows_like_a_perturbed_fp64_run():
+    """Reduced nonlinear case (a0 = 2, n0 = 0.01, 256 x 64): the FP32 path against FP64 beside
+    an FP64 run whose initial particle state is rounded to FP32 once.  The wake of this run is
+    dynamically unstable: both differences grow exponentially at the same rate (a systematic
+    FP32 error would not follow the instability's rate), the wake holds the 1e-3 bar early on,
+    and peak |A|, which the instability does not amplify, holds it throughout."""
+    import bench
+    w = dataclasses.replace(C1, name="nonlinear", nx=256, nr=64, a0=2.0, w0=12.0, L=8.0, n0=0.01,
+                            sort_every=20)
+    s64, s64p, s32 = gpu_from(w), gpu_from(w), gpu_from(w, precision="fp32")
+    bench.round_state_to_fp32(s64p)
+    s64.upload_particles(s64.particles())        # the same dump/upload round trip on both FP64 runs
+    steps, e32, ep, a32 = [], [], [], []
+    for k in range(16):
+        for s in (s64, s64p, s32):
+            s.step(25)
+        e = s64.ex_axis()
+        n = np.linalg.norm(e)
+        steps.append(25 * (k + 1))
+        e32.append(float(np.linalg.norm(s32.ex_axis() - e) / n))
+        ep.append(float(np.linalg.norm(s64p.ex_axis() - e) / n))
+        a32.append(abs(s32.a_abs_max() / s64.a_abs_max() - 1))
+    assert e32[3] <= 1e-3, e32[:4]                               # step 100
+    assert max(a32) <= 1e-3, a32
+    r32 = bench.growth_rate(steps, e32, last=325)["rate"]
+    rp = bench.growth_rate(steps, ep, last=325)["rate"]
+    assert r32 and rp and r32 > 0.01 and rp > 0.01, (r32, rp, e32, ep)
+    assert 1 / 1.6 < r32 / rp < 1.6, (r32, rp)
