@@ -203,6 +203,27 @@ __device__ __forceinline__ float gather_q(const float2 *__restrict__ G, const Ge
     return (1.f - f) * (1.f - gw) * c0.x + f * (1.f - gw) * c1.x + (1.f - f) * gw * c0.y + f * gw * c1.y;
 }
 
+// A (Phi, dPhi/dx, dPhi/dr) record through the read-only data path (the array is not written
+// during the pass; measured 5 % off FP32 pass A against plain loads).
+__device__ __forceinline__ Q4<float> ldg_q4(const Q4<float> *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    Q4<float> q;
+    q.phi = v.x;
+    q.gx = v.y;
+    q.gr = v.z;
+    q.pad = v.w;
+    return q;
+}
+__device__ __forceinline__ Q4<double> ldg_q4(const Q4<double> *p) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p)), v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    Q4<double> q;
+    q.phi = v0.x;
+    q.gx = v0.y;
+    q.gr = v1.x;
+    q.pad = v1.y;
+    return q;
+}
+
 // Results of pass A for one particle: its susceptibility deposit (four primal nodes from b,
 // row factors applied, with a bound on their size) and its new momentum.
 template <class R> struct AOut {
@@ -240,8 +261,8 @@ __device__ __forceinline__ AOut<R> a_particle(const SimDev<R> &S, const Geo &geo
     const int b = geo.at(off, L.ip, L.jp);
     const R wx0 = (R)1 - L.fp, wr0 = (R)1 - L.gp;
     const R w00 = wx0 * wr0, w10 = L.fp * wr0, w01 = wx0 * L.gp, w11 = L.fp * L.gp;
-    const Q4<R> q00 = S.f.pg[b], q10 = S.f.pg[b + geo.P];
-    const Q4<R> q01 = S.f.pg[b + 1], q11 = S.f.pg[b + geo.P + 1];
+    const Q4<R> q00 = ldg_q4(S.f.pg + b), q10 = ldg_q4(S.f.pg + b + geo.P);
+    const Q4<R> q01 = ldg_q4(S.f.pg + b + 1), q11 = ldg_q4(S.f.pg + b + geo.P + 1);
     const R phg = w00 * q00.phi + w10 * q10.phi + w01 * q01.phi + w11 * q11.phi;
     const R gxg = w00 * q00.gx + w10 * q10.gx + w01 * q01.gx + w11 * q11.gx;
     const R grg = w00 * q00.gr + w10 * q10.gr + w01 * q01.gr + w11 * q11.gr;
@@ -439,10 +460,18 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
         const bool la = cur.ix.x != kDead, lb = cur.ix.y != kDead;
         const AOut<float> a = a_particle<float, true>(S, geo, off, shift, cur.ix.x, cur.ox.x, cur.y.x, cur.z.x,
                                                 m.px.x, m.py.x, m.pz.x, m.w.x);
-        if (la) { __stcs(P.px + k, a.px); __stcs(P.py + k, a.py); __stcs(P.pz + k, a.pz); }
         const AOut<float> b = a_particle<float, true>(S, geo, off, shift, cur.ix.y, cur.ox.y, cur.y.y, cur.z.y,
                                                 m.px.y, m.py.y, m.pz.y, m.w.y);
-        if (lb) { __stcs(P.px + k + 1, b.px); __stcs(P.py + k + 1, b.py); __stcs(P.pz + k + 1, b.pz); }
+        // the pair's new momenta as 8-byte stores (measured 5 % faster than storing each
+        // particle's as soon as it is pushed)
+        if (la && lb) {
+            __stcs(reinterpret_cast<float2 *>(P.px + k), make_float2(a.px, b.px));
+            __stcs(reinterpret_cast<float2 *>(P.py + k), make_float2(a.py, b.py));
+            __stcs(reinterpret_cast<float2 *>(P.pz + k), make_float2(a.pz, b.pz));
+        } else {
+            if (la) { __stcs(P.px + k, a.px); __stcs(P.py + k, a.py); __stcs(P.pz + k, a.pz); }
+            if (lb) { __stcs(P.px + k + 1, b.px); __stcs(P.py + k + 1, b.py); __stcs(P.pz + k + 1, b.pz); }
+        }
         const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
         double *const base_q[4] = {S.f.chi, S.f.chi, S.f.chi, S.f.chi};
         const int o[4] = {0, geo.P, 1, geo.P + 1};
