@@ -50,17 +50,20 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
     S.f.btn[id] = btn_here;
     if constexpr (sizeof(R) == 4) {
         // radial pairs for the FP32 gathers (nodes i in [-1, nx+1], j in [-1, nr]).  E is not
-        // written by this kernel, so a thread reads its upper neighbour; B is updated in place,
-        // so B^n of node (i, j) is stored by its own thread into both records that hold it:
-        // (i, j).x and (i, j-1).y (separate 4-byte words, no two threads write the same one).
+        // written by this kernel outside column -1, so a thread reads its upper neighbour; the
+        // column -1, which this kernel zeroes, gets zero pairs without reading it.  B is updated
+        // in place, so B^n of node (i, j) is stored by its own thread into both records that
+        // hold it: (i, j).x and (i, j-1).y (separate 4-byte words, no two threads write the
+        // same one).
         if (i >= -1 && i <= g.nx + 1 && j <= g.nr + 1) {
             float *bq = reinterpret_cast<float *>(S.f.btq);
             bq[2 * (long long)id] = btn_here;
             bq[2 * (long long)id - 1] = btn_here;   // (i, j-1).y; for j = 0 that of row -1
             if (j <= g.nr) {
-                const R ex0 = S.f.ex[id], er0 = S.f.er[id];
-                S.f.exq[id] = make_float2(ex0, S.f.ex[id + 1]);
-                S.f.erq[id] = make_float2(er0, S.f.er[id + 1]);
+                const bool guard = i == -1;
+                const R ex0 = guard ? (R)0 : S.f.ex[id], er0 = guard ? (R)0 : S.f.er[id];
+                S.f.exq[id] = make_float2(ex0, guard ? (R)0 : S.f.ex[id + 1]);
+                S.f.erq[id] = make_float2(er0, guard ? (R)0 : S.f.er[id + 1]);
                 if (j == 0) {   // row -1: the odd mirror (read for Er and Btheta only)
                     S.f.exq[id - 1] = make_float2(-ex0, ex0);
                     S.f.erq[id - 1] = make_float2(-er0, er0);
