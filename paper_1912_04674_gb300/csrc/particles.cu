@@ -56,8 +56,8 @@ __device__ __forceinline__ R gather4(const R *__restrict__ F, const Geo &geo, in
     const R l0 = __ldg(F + b), l1 = __ldg(F + b + geo.P);
     const R f01 = __ldg(F + b + up), f11 = __ldg(F + b + geo.P + up);
     const R f00 = ghost ? -l0 : l0, f10 = ghost ? -l1 : l1;
-    return ((R)1 - f) * ((R)1 - gw) * f00 + f * ((R)1 - gw) * f10 + ((R)1 - f) * gw * f01 +
-           f * gw * f11;
+    const R lo = f00 + f * (f10 - f00), hi = f01 + f * (f11 - f01);
+    return lo + gw * (hi - lo);
 }
 
 
@@ -200,7 +200,8 @@ __device__ __forceinline__ float gather_q(const float2 *__restrict__ G, const Ge
                                           int j, float gw) {
     const int b = geo.at(off, i, j);
     const float2 c0 = __ldg(G + b), c1 = __ldg(G + b + geo.P);
-    return (1.f - f) * (1.f - gw) * c0.x + f * (1.f - gw) * c1.x + (1.f - f) * gw * c0.y + f * gw * c1.y;
+    const float lo = c0.x + f * (c1.x - c0.x), hi = c0.y + f * (c1.y - c0.y);
+    return lo + gw * (hi - lo);
 }
 
 // A (Phi, dPhi/dx, dPhi/dr) record through the read-only data path (the array is not written
