@@ -40,7 +40,7 @@ PARTICLE_BYTES = {
 # FP64 operations per particle of the FP64 particle passes (FMA counted as two), from the
 # ncu op counts of one launch divided by its particles; the FP64 path is bound by the FP64
 # pipe, whose rate is measured on the device (fp64_peak) and is 1.25 TFLOP/s nominal.
-FP64_FLOPS_PER_PARTICLE = {"pass_a": 236, "pass_b": 145}
+FP64_FLOPS_PER_PARTICLE = {"pass_a": 221, "pass_b": 127}
 FP64_NOMINAL_TFLOPS = 1.25
 
 

@@ -109,7 +109,7 @@ Layout make_layout(const lpic_grid_params *g, lpic_precision prec) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
     L.desc = take(sizeof(Desc));
-    L.tab = take((size_t)NTAB * L.P * rs);
+    L.tab = take((size_t)NTAB * L.P * rs + kAxisFactors * sizeof(double));
     // ex er bt btn phih (R), pg (4R), exq erq (2R, FP32 only), a0 a1 (2R), chi jx jr dq
     // (double), [14-16 filter], btq (2R, FP32 only)
     const bool paired = prec != LPIC_FP64;
@@ -517,6 +517,13 @@ lpic_status lpic_init_grid(lpic_ctx **out, const lpic_grid_params *g, lpic_preci
         e = prec == LPIC_FP64
                 ? cudaMemcpyAsync(c->buf + L.tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->st)
                 : cudaMemcpyAsync(c->buf + L.tab, tabf.data(), tabf.size() * 4, cudaMemcpyHostToDevice, c->st);
+    // the FP64 factors of the axis rows, after the working-precision tables
+    static_assert(kAxisFactors == 2, "axis factors: 1/V_chi,0 and 1/(dt V_0/dx)");
+    const double axis[kAxisFactors] = {row_ichi(c->ph, 0), row_ijx(c->ph, 0)};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->buf + L.tab + (size_t)NTAB * L.P * (prec == LPIC_FP64 ? 8 : 4), axis, sizeof axis,
+                            cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // `axis` lives on this stack frame
     if (e != cudaSuccess) {
         g_thread_err = std::string("lpic_init_grid: ") + cudaGetErrorString(e);
         if (c->h_desc) cudaFreeHost(c->h_desc);

@@ -187,7 +187,7 @@ template <class R> __device__ __forceinline__ void envelope_axis_node(const SimD
     const Kc<R> &K = S.k;
     double dre, dim;
     envelope_node<double>(c, A[g.at(off, i + 1, 0)], A[g.at(off, i - 1, 0)], A[id + 1], c,
-                          S.f.a[ab ^ 1][id], S.f.chi[id] * row_ichi(S.ph, 0), true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
+                          S.f.a[ab ^ 1][id], S.f.chi[id] * axis_factor(K.tab, g.P, 0), true, K.d_idx2, K.d_idr2, 0.0, K.d_hidx,
                           K.d_dt, K.d_dt2, K.d_envp, K.d_envpt, dre, dim);
     envelope_store<R>(S, id, ab, c, (R)dre, (R)dim);
 }
@@ -214,7 +214,7 @@ template <class R> __device__ __forceinline__ void ampere_tile(const SimDev<R> &
             S.f.ex[id] = (R)0;
         } else if (j == 0) {  // axis row in FP64
             double curl = S.k.d_4idr * (double)S.f.bt[id];
-            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jxu[id] * row_ijx(S.ph, 0)));
+            S.f.ex[id] = (R)((double)S.f.ex[id] + S.k.d_dt * (curl - S.f.jxu[id] * axis_factor(S.k.tab, g.P, 1)));
         } else {
             R curl = S.k.tab[T_AMPP * g.P + j] * S.f.bt[id] - S.k.tab[T_AMPM * g.P + j] * S.f.bt[id - 1];
             S.f.ex[id] += dt * (curl - from_acc<R>(S.f.jxu[id]) * S.k.tab[T_JX * g.P + j]);

@@ -130,6 +130,13 @@ __host__ __device__ __forceinline__ double row_ijr(const Phys &ph, int j) {
     return (1.0 / ph.dt) / (2.0 * kPi * (j + 0.5) * ph.dr * ph.dx);
 }
 
+// The FP64 factors of the axis rows (envelope: 1/V_chi,0; Ampere: 1/(dt V_0/dx)) follow the
+// working-precision row tables in device memory (FP64 divisions are slow on this part).
+constexpr int kAxisFactors = 2;
+template <class R> __device__ __forceinline__ double axis_factor(const R *tab, int P, int which) {
+    return reinterpret_cast<const double *>(tab + (size_t)NTAB * P)[which];
+}
+
 // Constants of one simulation, computed on the host (FP64 is a slow pipe on this part,
 // so no kernel derives them per thread).
 template <class R> struct Kc {
