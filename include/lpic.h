@@ -197,7 +197,10 @@ lpic_status lpic_diagnose_async(lpic_ctx *ctx, lpic_diag_kind kind, void *host_o
  * LPIC_DIAG_EX/ER/BT/A/AM (exact sizes), LPIC_DIAG_PARTICLES (7n doubles: replaces the
  * particle set by n particles, ids reset to 0..n-1), LPIC_DIAG_PARTICLE_IDS (n ids for the
  * current set) and LPIC_DIAG_COUNTERS (step and shift; the other two entries are ignored).
- * Synchronises the context stream. */
+ * Page-locked host memory that the device can address (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor) is read by the conversion kernels in place over the host link; other
+ * host memory goes through the library's staging area in chunks.  Synchronises the context
+ * stream. */
 lpic_status lpic_upload(lpic_ctx *ctx, lpic_diag_kind kind, const void *host_in, size_t bytes);
 
 /* Tracing.  Launches of every kernel family are always counted; while timing is enabled,

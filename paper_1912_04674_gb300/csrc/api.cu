@@ -857,6 +857,18 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
         if (e == cudaSuccess) e = cudaGetLastError();
         return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_upload");
     };
+    // Page-locked host memory the device can address (cudaHostAlloc / cudaHostRegister with
+    // unified addressing): the conversion kernels read it in place over the host link, in one
+    // pass, instead of through the staging area chunk by chunk.
+    const void *mapped = nullptr;
+    if (host_in) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, host_in) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
+        } else {
+            (void)cudaGetLastError();   // not a CUDA-known pointer: pageable memory
+        }
+    }
     switch (kind) {
     case LPIC_DIAG_COUNTERS: {
         if (bytes != 4 * sizeof(int64_t)) return c->fail(LPIC_EINVAL, "counters: 4 int64 expected");
@@ -880,6 +892,10 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
         }
         const size_t colb = (size_t)nj * sizeof(double) * (cp ? 2 : 1);
         if (bytes != colb * ni) return c->fail(LPIC_EINVAL, "upload: wrong size for this array");
+        if (mapped) {
+            c->dispatch([&](auto &S) { launch_upload_field(S, (int)kind, 0, ni, (const double *)mapped, c->st); });
+            return finish();
+        }
         const int per = (int)(c->stage_bytes / colb);
         for (int c0 = 0; c0 < ni; c0 += per) {
             const int c1 = c0 + per < ni ? c0 + per : ni;
@@ -892,9 +908,15 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
         if (bytes % (7 * sizeof(double))) return c->fail(LPIC_EINVAL, "particles: 7n doubles expected");
         const long long n = (long long)(bytes / (7 * sizeof(double)));
         if (n > c->g.particle_capacity) return c->fail(LPIC_EBUFSIZE, "more particles than capacity");
-        const int chunk = (int)(c->stage_bytes / 8);
+        const int chunk = mapped ? (int)(n > 0 ? n : 1) : (int)(c->stage_bytes / 8);
         for (int comp = 0; comp < 7; comp++)
             for (long long k0 = 0; k0 < n; k0 += chunk) {
+                if (mapped) {
+                    c->dispatch([&](auto &S) {
+                        launch_upload_particles(S, 0, (int)n, comp, (const double *)mapped + comp * n, c->st);
+                    });
+                    continue;
+                }
                 const long long k1 = k0 + chunk < n ? k0 + chunk : n;
                 if ((s = h2d(c->stage, (const double *)host_in + comp * n + k0, 8 * (size_t)(k1 - k0))) != LPIC_OK)
                     return s;
@@ -909,6 +931,12 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
         const long long n = (long long)(bytes / sizeof(uint64_t));
         if (bytes % 8 || n != c->h_desc->np)
             return c->fail(LPIC_EINVAL, "ids: one uint64 per particle slot expected");
+        if (mapped) {
+            c->dispatch([&](auto &S) {
+                launch_set_ids(S, nullptr, 0, (int)n, (const uint64_t *)mapped, nullptr, 1, c->st);
+            });
+            return finish();
+        }
         const int chunk = (int)(c->stage_bytes / 8);
         for (long long k0 = 0; k0 < n; k0 += chunk) {
             const long long k1 = k0 + chunk < n ? k0 + chunk : n;

@@ -281,3 +281,37 @@ def test_hand_placed_edge_particles_step_by_step(precision, tol):
     gone = [k for k in range(len(e["x"])) if int(e["id"][k]) not in ids]
     assert {7, 9, 10} <= set(gone), gone        # the r_max and back-edge removals happened
     assert 8 not in gone and 0 not in gone
+
+
+def test_upload_from_pinned_host_memory_matches_pageable():
+    """Uploads from page-locked host memory are read by the conversion kernels in place (no
+    staging); the state they leave must equal the staged upload of the same pageable data."""
+    import torch
+
+    w = dataclasses.replace(C1, name="pinned", nx=64, nr=32, a0=1.0, w0=10.0, L=6.0, n0=0.01)
+    src = gpu_from(w)
+    src.step(7)
+    parts = src.particles()
+    fields = {k: src.field(k) for k in ("ex", "er", "bt", "a", "am")}
+    c = src.counters()
+    raw = np.concatenate([parts[k] for k in ("x", "y", "z", "px", "py", "pz", "w")])
+    pinned_raw = torch.from_numpy(raw).pin_memory()
+    pinned_ids = torch.from_numpy(np.ascontiguousarray(parts["id"].view(np.int64))).pin_memory()
+    pinned_f = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in fields.items()}
+    a, b = gpu_from(w), gpu_from(w)
+    for sim in (a, b):
+        sim.upload_counters(c["step"], c["shift"])
+    for k, v in fields.items():
+        a.upload_field(k, v)                           # pageable: staged
+        b.upload_field(k, pinned_f[k].numpy())         # page-locked: read in place
+    a.upload_particles_raw(raw, parts["id"])
+    b.upload_particles_raw(pinned_raw.numpy(), pinned_ids.numpy().view(np.uint64))
+    for k in fields:
+        np.testing.assert_array_equal(a.field(k), b.field(k))
+    pa, pb = a.particles(), b.particles()
+    for k in pa:
+        np.testing.assert_array_equal(pa[k], pb[k])
+    a.step(3)
+    b.step(3)
+    for k in ("ex", "a", "chi", "jx"):
+        assert rel_err(b.field(k), a.field(k)) <= 1e-12
