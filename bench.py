@@ -274,31 +274,29 @@ def roofline(prof: dict, prec: str, alive: float, pk: dict, fp64pk: dict | None 
 
 
 def e2e_run(prec: str, k: int, settle_steps: int):
-    """Same metric through the public API with host buffers: upload of a settled state from
-    pinned host memory, then k steps, each step's on-axis wake read into pinned host memory
-    (double-buffered, lpic_diagnose_async) and consumed by the host while the next step
-    runs."""
+    """Same metric through the public API with host buffers: upload of a settled checkpoint
+    (counters, fields, the particle store in its native layout) from pinned host memory, then
+    k steps, each step's on-axis wake read into pinned host memory (double-buffered,
+    lpic_diagnose_async) and consumed by the host while the next step runs."""
     import numpy as np
     import torch
     sim = make_sim(prec)
     settle(sim, settle_steps)
-    parts = sim.particles()
+    c = sim.counters()
     fields = {n: sim.field(n) for n in ("ex", "er", "bt", "a", "am")}
-    # the inputs in pinned host memory, in the API's layouts (7n particle values, n ids, fields)
-    held = [torch.from_numpy(np.concatenate([parts[c] for c in ("x", "y", "z", "px", "py", "pz", "w")])).pin_memory(),
-            torch.from_numpy(np.ascontiguousarray(parts["id"])).pin_memory()]
+    # the inputs in pinned host memory, in the API's checkpoint layouts
+    held = [torch.from_numpy(sim.particles_native()).pin_memory()]
     held += [torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in fields.values()]
-    raw, ids = held[0].numpy(), held[1].numpy()
-    pinf = dict(zip(fields, (t.numpy() for t in held[2:])))
-    h2d = raw.nbytes + ids.nbytes + sum(v.nbytes for v in pinf.values())
-    alive = len(parts["x"])
+    blob = held[0].numpy()
+    pinf = dict(zip(fields, (t.numpy() for t in held[1:])))
+    h2d = blob.nbytes + sum(v.nbytes for v in pinf.values()) + 32
+    alive = c["alive"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    c = sim.counters()
     sim.upload_counters(c["step"], c["shift"])
     for n, v in pinf.items():
         sim.upload_field(n, v)
-    sim.upload_particles_raw(raw, ids)
+    sim.upload_particles_native(blob)
     d2h = 0
     bufs = [torch.zeros(sim.grid.nx, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
     evs = [torch.cuda.Event() for _ in range(2)]
@@ -315,11 +313,13 @@ def e2e_run(prec: str, k: int, settle_steps: int):
     seen += float(np.abs(bufs[(k - 1) % 2]).max())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    sim_itemsize = sim.native_itemsize
     sim.close()
     return {"value": alive * k / dt, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d / k),
             "d2h_bytes_per_step": int(d2h / k), "steps": k, "wake_read": seen > 0,
-            "note": "upload of a settled state amortised over the steps; every step's wake read "
-                    "back to pinned host memory and consumed while the next step runs"}
+            "note": "upload of a settled checkpoint (counters, fields, native particle store: "
+                    f"{12 + 7 * sim_itemsize} B per electron) amortised over the steps; every step's "
+                    "wake read back to pinned host memory and consumed while the next step runs"}
 
 
 def beam_compare(s64, s32, s64b):

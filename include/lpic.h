@@ -125,7 +125,17 @@ typedef enum {
                                  /* chi, J, dQ: deposits of the last step, on that step's window
                                     (before its moving-window shift)                        */
     LPIC_DIAG_PARTICLES = 20,    /* 7 x n doubles, SoA: x(lab), y, z, px, py, pz, w          */
-    LPIC_DIAG_PARTICLE_IDS = 21  /* n uint64 ids, same order as LPIC_DIAG_PARTICLES          */
+    LPIC_DIAG_PARTICLE_IDS = 21, /* n uint64 ids, same order as LPIC_DIAG_PARTICLES          */
+    LPIC_DIAG_PARTICLES_NATIVE = 22
+                                 /* the particle store as the context holds it (checkpoint
+                                    form), same particles and order as LPIC_DIAG_PARTICLES:
+                                    n uint64 ids, then 7 blocks of n values in the working
+                                    precision (float for LPIC_FP32_MIXED, double for
+                                    LPIC_FP64): in-cell x offset in [0, 1), y, z, px, py, pz,
+                                    w; then n int32 lab cell indices (x = (cell + offset) dx).
+                                    12 + 7 x 4 = 40 bytes per electron in FP32_MIXED, 68 in
+                                    FP64; every block starts aligned to its element size.
+                                    Dump and upload are bit-exact.                          */
 } lpic_diag_kind;
 
 /* Stability and consistency check of the parameters, host only (needs no GPU).
@@ -196,11 +206,17 @@ lpic_status lpic_diagnose_async(lpic_ctx *ctx, lpic_diag_kind kind, void *host_o
  * (checkpoint restore, or starting from another implementation's state).  Accepts
  * LPIC_DIAG_EX/ER/BT/A/AM (exact sizes), LPIC_DIAG_PARTICLES (7n doubles: replaces the
  * particle set by n particles, ids reset to 0..n-1), LPIC_DIAG_PARTICLE_IDS (n ids for the
- * current set) and LPIC_DIAG_COUNTERS (step and shift; the other two entries are ignored).
+ * current set), LPIC_DIAG_PARTICLES_NATIVE (n electrons in the context's own layout and
+ * precision, ids included: a dump of this kind restores the particle store bit for bit) and
+ * LPIC_DIAG_COUNTERS (step and shift; the other two entries are ignored).  A particle upload
+ * marks electrons outside the window or at r >= r_max as removed, and restarts the sort
+ * cadence (the next counting sort comes sort_every steps later).  Field dumps and uploads are
+ * exact in both precisions (FP32 values pass through FP64 unchanged), so the field kinds, the
+ * native particles and the counters together are a checkpoint.
  * Page-locked host memory that the device can address (cudaHostAlloc, cudaHostRegister, a
- * pinned torch tensor) is read by the conversion kernels in place over the host link; other
- * host memory goes through the library's staging area in chunks.  Synchronises the context
- * stream. */
+ * pinned torch tensor) and that is 8-byte aligned is read by the conversion kernels in place
+ * over the host link; other host memory goes through the library's staging area in chunks.
+ * Synchronises the context stream. */
 lpic_status lpic_upload(lpic_ctx *ctx, lpic_diag_kind kind, const void *host_in, size_t bytes);
 
 /* Tracing.  Launches of every kernel family are always counted; while timing is enabled,

@@ -838,6 +838,26 @@ lpic_status lpic_diagnose(lpic_ctx *c, lpic_diag_kind kind, void *host_out, size
             }
         return LPIC_OK;
     }
+    case LPIC_DIAG_PARTICLES_NATIVE: {
+        c->dispatch([&](auto &S) { launch_alive_index(S, launch_cap(c), c->key, c->blockcnt, c->icount, c->st); });
+        int n = 0;
+        if ((s = copy_back(&n, c->icount, sizeof n)) != LPIC_OK) return s;
+        const size_t es = c->prec == LPIC_FP64 ? 8 : 4;
+        if (!need((12 + 7 * es) * (size_t)n)) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
+        const int chunk = (int)(c->stage_bytes / 8);
+        size_t at = 0;
+        for (int comp = 0; comp < 9; comp++) {
+            const size_t esz = comp == 0 ? 8 : comp == 8 ? 4 : es;
+            for (int k0 = 0; k0 < n; k0 += chunk) {
+                const int k1 = k0 + chunk < n ? k0 + chunk : n;
+                c->dispatch([&](auto &S) { launch_native_particles(S, c->key, k0, k1, comp, c->stage, 0, c->st); });
+                if ((s = copy_back((char *)host_out + at + esz * k0, c->stage, esz * (size_t)(k1 - k0))) != LPIC_OK)
+                    return s;
+            }
+            at += esz * (size_t)n;
+        }
+        return LPIC_OK;
+    }
     }
     return c->fail(LPIC_EINVAL, "unknown diagnostic kind");
 }
@@ -859,12 +879,14 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
     };
     // Page-locked host memory the device can address (cudaHostAlloc / cudaHostRegister with
     // unified addressing): the conversion kernels read it in place over the host link, in one
-    // pass, instead of through the staging area chunk by chunk.
+    // pass, instead of through the staging area chunk by chunk.  Only 8-byte aligned buffers:
+    // the kernels read doubles and 64-bit ids from it.
     const void *mapped = nullptr;
     if (host_in) {
         cudaPointerAttributes pa{};
         if (cudaPointerGetAttributes(&pa, host_in) == cudaSuccess) {
-            if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer && (uintptr_t)pa.devicePointer % 8 == 0)
+                mapped = pa.devicePointer;
         } else {
             (void)cudaGetLastError();   // not a CUDA-known pointer: pageable memory
         }
@@ -922,6 +944,36 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
                     return s;
                 c->dispatch([&](auto &S) { launch_upload_particles(S, (int)k0, (int)k1, comp, (const double *)c->stage, c->st); });
             }
+        c->dispatch([&](auto &S) { launch_finish_upload(S, (int)n, c->st); });
+        c->np_upper = n;
+        c->since_sort = 0;
+        return finish();
+    }
+    case LPIC_DIAG_PARTICLES_NATIVE: {
+        const size_t es = c->prec == LPIC_FP64 ? 8 : 4, per = 12 + 7 * es;
+        if (bytes % per) return c->fail(LPIC_EINVAL, "native particles: 12 + 7 x element bytes per electron expected");
+        const long long n = (long long)(bytes / per);
+        if (n > c->g.particle_capacity) return c->fail(LPIC_EBUFSIZE, "more particles than capacity");
+        const int chunk = (int)(c->stage_bytes / 8);
+        size_t at = 0;
+        for (int comp = 0; comp < 9; comp++) {
+            const size_t esz = comp == 0 ? 8 : comp == 8 ? 4 : es;
+            if (mapped) {
+                c->dispatch([&](auto &S) {
+                    launch_native_particles(S, nullptr, 0, (int)n, comp, (char *)mapped + at, 1, c->st);
+                });
+            } else {
+                for (long long k0 = 0; k0 < n; k0 += chunk) {
+                    const long long k1 = k0 + chunk < n ? k0 + chunk : n;
+                    if ((s = h2d(c->stage, (const char *)host_in + at + esz * k0, esz * (size_t)(k1 - k0))) != LPIC_OK)
+                        return s;
+                    c->dispatch([&](auto &S) {
+                        launch_native_particles(S, nullptr, (int)k0, (int)k1, comp, c->stage, 1, c->st);
+                    });
+                }
+            }
+            at += esz * (size_t)n;
+        }
         c->dispatch([&](auto &S) { launch_finish_upload(S, (int)n, c->st); });
         c->np_upper = n;
         c->since_sort = 0;

@@ -333,6 +333,40 @@ __global__ void k_upload_particles(SimDev<R> S, int k0, int k1, int comp, const 
     }
 }
 
+// The particle store in its own layout (LPIC_DIAG_PARTICLES_NATIVE), component comp of
+// particles [k0, k1): 0 the id (uint64), 1-7 the in-cell offset, y, z, px, py, pz, w (R), 8
+// the lab cell (int32).  mode 0: buf[t] = component of slot idx[k0+t] (dump); mode 1: the
+// component of slot k0+t = buf[t] (upload).  Plain copies of the stored bits.
+template <class R> __device__ __forceinline__ R *native_comp(const Parts<R> &P, int comp) {
+    switch (comp) {
+    case 1: return P.ox;
+    case 2: return P.y;
+    case 3: return P.z;
+    case 4: return P.px;
+    case 5: return P.py;
+    case 6: return P.pz;
+    default: return P.w;
+    }
+}
+template <class R>
+__global__ void k_native(SimDev<R> S, const int *idx, int k0, int k1, int comp, void *buf, int mode) {
+    const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
+    R *a = native_comp<R>(P, comp);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k1 - k0; t += gridDim.x * blockDim.x) {
+        const int k = mode == 0 ? idx[k0 + t] : k0 + t;
+        if (comp == 0) {
+            if (mode == 0) static_cast<uint64_t *>(buf)[t] = P.id[k];
+            else P.id[k] = static_cast<const uint64_t *>(buf)[t];
+        } else if (comp == 8) {
+            if (mode == 0) static_cast<int *>(buf)[t] = P.ix[k];
+            else P.ix[k] = static_cast<const int *>(buf)[t];
+        } else {
+            if (mode == 0) static_cast<R *>(buf)[t] = a[k];
+            else a[k] = static_cast<const R *>(buf)[t];
+        }
+    }
+}
+
 // mode 0: out[t] = id[idx[k0+t]] (dump);  mode 1: id[k0+t] = stage[t] (upload)
 template <class R>
 __global__ void k_ids(SimDev<R> S, const int *idx, int k0, int k1, const uint64_t *stage,
@@ -432,6 +466,11 @@ void launch_set_ids(const SimDev<R> &S, const int *idx, int k0, int k1, const ui
                     uint64_t *out, int mode, cudaStream_t st) {
     k_ids<R><<<pgrid(k1 - k0), TPB, 0, st>>>(S, idx, k0, k1, stage, out, mode);
 }
+template <class R>
+void launch_native_particles(const SimDev<R> &S, const int *idx, int k0, int k1, int comp, void *buf, int mode,
+                             cudaStream_t st) {
+    if (k1 > k0) k_native<R><<<pgrid(k1 - k0), TPB, 0, st>>>(S, idx, k0, k1, comp, buf, mode);
+}
 template <class R> void launch_finish_upload(const SimDev<R> &S, int n, cudaStream_t st) {
     k_finish_upload<R><<<pgrid(n), TPB, 0, st>>>(S, n);
 }
@@ -452,6 +491,8 @@ template <class R> void launch_finish_upload(const SimDev<R> &S, int n, cudaStre
     template void launch_alive_index<R>(const SimDev<R> &, int, int *, int *, int *, cudaStream_t); \
     template void launch_dump_particles<R>(const SimDev<R> &, const int *, int, int, int, double *, \
                                            cudaStream_t);                                       \
+    template void launch_native_particles<R>(const SimDev<R> &, const int *, int, int, int, void *, int, \
+                                             cudaStream_t);                                     \
     template void launch_upload_particles<R>(const SimDev<R> &, int, int, int, const double *,  \
                                              cudaStream_t);                                     \
     template void launch_set_ids<R>(const SimDev<R> &, const int *, int, int, const uint64_t *, \

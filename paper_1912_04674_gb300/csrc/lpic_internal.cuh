@@ -405,6 +405,8 @@ template <class R> void launch_alive_index(const SimDev<R> &S, int np_upper, int
                                            int *blockcnt, int *d_count, cudaStream_t st);
 template <class R> void launch_dump_particles(const SimDev<R> &S, const int *idx, int k0, int k1,
                                               int comp, double *stage, cudaStream_t st);
+template <class R> void launch_native_particles(const SimDev<R> &S, const int *idx, int k0, int k1,
+                                                int comp, void *buf, int mode, cudaStream_t st);
 template <class R> void launch_upload_particles(const SimDev<R> &S, int k0, int k1, int comp,
                                                 const double *stage, cudaStream_t st);
 template <class R> void launch_set_ids(const SimDev<R> &S, const int *idx, int k0, int k1,

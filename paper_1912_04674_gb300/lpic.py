@@ -28,8 +28,28 @@ LPIC_FP64, LPIC_FP32_MIXED = 0, 1
 PRECISION = {"fp64": LPIC_FP64, "fp32": LPIC_FP32_MIXED, "fp32_mixed": LPIC_FP32_MIXED}
 DIAG = {"ex_axis": 0, "a_abs_max": 1, "waist": 2, "cont_residual": 3, "accel_energy": 4,
         "counters": 5, "beam": 6, "ex": 10, "er": 11, "bt": 12, "a": 13, "am": 14, "chi": 15, "jx": 16,
-        "jr": 17, "dq": 18, "particles": 20, "particle_ids": 21}
+        "jr": 17, "dq": 18, "particles": 20, "particle_ids": 21, "particles_native": 22}
 PART_COMPONENTS = ("x", "y", "z", "px", "py", "pz", "w")
+NATIVE_COMPONENTS = ("ox", "y", "z", "px", "py", "pz", "w")   # in-cell x offset, then as above
+
+
+def split_native(raw: np.ndarray, itemsize: int) -> dict:
+    """Views of the blocks of a LPIC_DIAG_PARTICLES_NATIVE buffer: id (uint64), the seven
+    working-precision components (float32 for itemsize 4, float64 for 8) and the lab cell
+    index (int32)."""
+    b = np.ascontiguousarray(raw).view(np.uint8)
+    per = 12 + 7 * itemsize
+    if b.size % per:
+        raise ValueError(f"native particle buffer: {b.size} bytes is not a multiple of {per}")
+    n = b.size // per
+    ft = np.float32 if itemsize == 4 else np.float64
+    out = {"id": b[: 8 * n].view(np.uint64)}
+    at = 8 * n
+    for k in NATIVE_COMPONENTS:
+        out[k] = b[at: at + itemsize * n].view(ft)
+        at += itemsize * n
+    out["cell"] = b[at: at + 4 * n].view(np.int32)
+    return out
 
 
 class LpicError(RuntimeError):
@@ -475,6 +495,16 @@ class Simulation:
         out["id"] = self._diag("particle_ids", np.uint64)
         return out
 
+    @property
+    def native_itemsize(self) -> int:
+        """Bytes of one working-precision value (4 for FP32_MIXED, 8 for FP64)."""
+        return 8 if self.precision == LPIC_FP64 else 4
+
+    def particles_native(self) -> np.ndarray:
+        """The particle store as the context holds it (LPIC_DIAG_PARTICLES_NATIVE), as bytes;
+        split_native(raw, self.native_itemsize) gives its blocks.  Bit-exact checkpoint form."""
+        return self._diag("particles_native", np.uint8)
+
     # -- uploads -----------------------------------------------------------------------------
     def upload_field(self, name: str, arr: np.ndarray):
         a = np.ascontiguousarray(arr)       # no copy of a contiguous array of the right type
@@ -499,6 +529,12 @@ class Simulation:
         if ids is not None and raw.size:
             ids = np.ascontiguousarray(ids, dtype=np.uint64)
             lpic_upload(self.ctx, DIAG["particle_ids"], ids.ctypes.data_as(C.c_void_p), ids.nbytes)
+
+    def upload_particles_native(self, raw: np.ndarray):
+        """Replace the particle store by a LPIC_DIAG_PARTICLES_NATIVE buffer of the same
+        precision (ids included), bit for bit; no host copy is made of a contiguous buffer."""
+        b = np.ascontiguousarray(raw)
+        lpic_upload(self.ctx, DIAG["particles_native"], b.ctypes.data_as(C.c_void_p), b.nbytes)
 
     def inject_bunch(self, parts: dict, gamma: float):
         """Append a relativistic electron bunch (x lab, y, z, px, py, pz, w) and add its

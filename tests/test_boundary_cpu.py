@@ -106,3 +106,42 @@ def test_memory_plan_and_capacity(L):
         # two particle buffers dominate: 68 B (FP64) / 40 B (FP32) per slot
         assert b64 > 2 * 68 * gs.particle_capacity and b32 > 2 * 40 * gs.particle_capacity
         assert b32 < b64 < 2 * 68 * gs.particle_capacity + 400e6
+
+
+def test_diagnostic_kinds_match_the_header(L):
+    """The binding's kind numbers are the header's lpic_diag_kind values (compiled by gcc)."""
+    import tempfile
+    names = {k: "LPIC_DIAG_" + k.upper() for k in L.DIAG}
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "k.c")
+        with open(src, "w") as f:
+            f.write('#include "lpic.h"\n#include <stdio.h>\nint main(void){\n')
+            for c_name in names.values():
+                f.write(f'printf("%d\\n", (int){c_name});\n')
+            f.write("return 0;}\n")
+        exe = os.path.join(d, "k")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert got == list(L.DIAG.values())
+
+
+@pytest.mark.parametrize("itemsize", [4, 8])
+def test_native_particle_layout_split(L, itemsize):
+    """LPIC_DIAG_PARTICLES_NATIVE: ids, seven working-precision blocks, then int32 cells, each
+    block aligned to its element size."""
+    n = 5
+    ft = np.float32 if itemsize == 4 else np.float64
+    ids = np.arange(100, 100 + n, dtype=np.uint64)
+    comps = {k: (np.arange(n) + 10 * q).astype(ft) for q, k in enumerate(L.NATIVE_COMPONENTS)}
+    cells = np.arange(-2, n - 2, dtype=np.int32)
+    blob = np.concatenate([ids.view(np.uint8)] + [comps[k].view(np.uint8) for k in L.NATIVE_COMPONENTS]
+                          + [cells.view(np.uint8)])
+    assert blob.nbytes == (12 + 7 * itemsize) * n
+    p = L.split_native(blob, itemsize)
+    np.testing.assert_array_equal(p["id"], ids)
+    for k in L.NATIVE_COMPONENTS:
+        np.testing.assert_array_equal(p[k], comps[k])
+        assert p[k].dtype == ft
+    np.testing.assert_array_equal(p["cell"], cells)
+    with pytest.raises(ValueError):
+        L.split_native(blob[:-1], itemsize)
