@@ -912,7 +912,7 @@ def main():
                     help="jobs of the served-scan leg (0 skips it)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU legs")
-    ap.add_argument("--only", choices=("batch", "large", "filter", "bunch", "slabs"), default=None,
+    ap.add_argument("--only", choices=("batch", "large", "filter", "bunch", "slabs", "e2e"), default=None,
                     help="run one leg alone and print its object (a profiling run, not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -938,6 +938,9 @@ def main():
         return
     if args.only == "slabs":
         print(json.dumps({"profile_run": True, "slabs": slab_leg()}))
+        return
+    if args.only == "e2e":
+        print(json.dumps({"profile_run": True, "e2e": e2e_run("fp32", args.steps, args.settle)}))
         return
     run_ours(args)
 
