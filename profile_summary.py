@@ -3,12 +3,14 @@
     python profile_summary.py launches <launches.csv> <title> <command>
     python profile_summary.py capture <report.ncu-rep> <title> <command>
     python profile_summary.py traffic <report.ncu-rep> <precision>
+    python profile_summary.py mix <report.ncu-rep> <title> <command> <particles>
 
 `launches`: per kernel, the launch count, total time and share of a
 `--metrics gpu__time_duration.sum` launch list (cold-cache, serialised: compare shares).
 `capture`: the key counters of a `--set full` capture.  `traffic`: writes the DRAM bytes
 per launch of pass_a / pass_b into profiles/traffic.json, keyed by the kernels' source hash
-(the benchmark reports it only while the sources are unchanged).
+(the benchmark reports it only while the sources are unchanged).  `mix`: the instruction
+classes of a capture of the op-class counters, per particle (thread instructions / particles).
 """
 from __future__ import annotations
 
@@ -125,6 +127,47 @@ def capture(rep, title, command, how="--set full"):
     return "\n".join(out) + "\n"
 
 
+MIX = [
+    ("sm__sass_thread_inst_executed_ops_fadd_fmul_ffma_pred_on.sum", "FP32 add/mul/fma"),
+    ("sm__sass_thread_inst_executed_ops_fadd2_fmul2_ffma2_pred_on.sum", "FP32 paired add/mul/fma"),
+    ("sm__sass_thread_inst_executed_op_fp32_pred_on.sum", "all FP32"),
+    ("sm__sass_thread_inst_executed_op_integer_pred_on.sum", "integer"),
+    ("sm__sass_thread_inst_executed_op_bit_pred_on.sum", "bit"),
+    ("sm__sass_thread_inst_executed_op_conversion_pred_on.sum", "conversion"),
+    ("sm__sass_thread_inst_executed_op_memory_pred_on.sum", "memory"),
+    ("sm__sass_thread_inst_executed_op_control_pred_on.sum", "control"),
+    ("sm__sass_thread_inst_executed_op_inter_thread_communication_pred_on.sum", "shuffle/vote/reduce"),
+    ("sm__sass_thread_inst_executed_op_misc_pred_on.sum", "misc"),
+    ("sm__sass_thread_inst_executed_op_uniform_pred_on.sum", "uniform"),
+    ("sm__sass_thread_inst_executed_op_fp64_pred_on.sum", "FP64"),
+    ("smsp__thread_inst_executed.sum", "all thread instructions"),
+    ("smsp__inst_executed.sum", "warp instructions"),
+]
+
+
+def mix(rep, title, command, particles):
+    hdr, units, rows = raw(rep)
+    n = float(particles)
+    names = [short(r[hdr.index("Kernel Name")]) for r in rows]
+    out = [f"# {title}", "", f"Command: `{command}`", "",
+           "ncu op-class counters (`--metrics <the counters below> --clock-control none`), per particle",
+           f"({int(n)} particles per launch): thread instructions whose predicate was on, by class;",
+           "the last two rows count every executed instruction.", "",
+           "| class | " + " | ".join(names) + " |", "|---|" + "---|" * len(names)]
+    for key, label in MIX:
+        if key in hdr:
+            i = hdr.index(key)
+            out.append(f"| {label} | " + " | ".join(f"{float(r[i].replace(',', '')) / n:.2f}" for r in rows) + " |")
+    for key, label in (("gpu__time_duration.sum", "duration"),
+                       ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+                       ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active %"),
+                       ("launch__registers_per_thread", "registers/thread")):
+        if key in hdr:
+            i = hdr.index(key)
+            out.append(f"| {label} ({units[i]}) | " + " | ".join(r[i] for r in rows) + " |")
+    return "\n".join(out) + "\n"
+
+
 def traffic(rep, prec):
     sys.path.insert(0, ROOT)
     import bench
@@ -148,5 +191,7 @@ if __name__ == "__main__":
         print(launches(*sys.argv[2:5]))
     elif mode == "capture":
         print(capture(*sys.argv[2:5], *(sys.argv[5:6] or ["--set full"])))
+    elif mode == "mix":
+        print(mix(*sys.argv[2:6]))
     else:
         print(traffic(*sys.argv[2:4]))
