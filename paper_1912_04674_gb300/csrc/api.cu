@@ -954,26 +954,20 @@ lpic_status lpic_upload(lpic_ctx *c, lpic_diag_kind kind, const void *host_in, s
         if (bytes % per) return c->fail(LPIC_EINVAL, "native particles: 12 + 7 x element bytes per electron expected");
         const long long n = (long long)(bytes / per);
         if (n > c->g.particle_capacity) return c->fail(LPIC_EBUFSIZE, "more particles than capacity");
-        const int chunk = (int)(c->stage_bytes / 8);
-        size_t at = 0;
-        for (int comp = 0; comp < 9; comp++) {
-            const size_t esz = comp == 0 ? 8 : comp == 8 ? 4 : es;
-            if (mapped) {
-                c->dispatch([&](auto &S) {
-                    launch_native_particles(S, nullptr, 0, (int)n, comp, (char *)mapped + at, 1, c->st);
-                });
-            } else {
-                for (long long k0 = 0; k0 < n; k0 += chunk) {
-                    const long long k1 = k0 + chunk < n ? k0 + chunk : n;
-                    if ((s = h2d(c->stage, (const char *)host_in + at + esz * k0, esz * (size_t)(k1 - k0))) != LPIC_OK)
-                        return s;
-                    c->dispatch([&](auto &S) {
-                        launch_native_particles(S, nullptr, (int)k0, (int)k1, comp, c->stage, 1, c->st);
-                    });
-                }
+        // the blocks are the particle arrays themselves: plain copies into slots [0, n) of the
+        // current buffer (the copy engines move them; no conversion kernel)
+        const int pb = c->h_desc->pbuf;
+        c->dispatch([&](auto &S) {
+            const auto &P = S.p[pb ? 1 : 0];
+            void *const dst[9] = {P.id, P.ox, P.y, P.z, P.px, P.py, P.pz, P.w, P.ix};
+            size_t at = 0;
+            for (int comp = 0; comp < 9 && s == LPIC_OK; comp++) {
+                const size_t b = (comp == 0 ? 8 : comp == 8 ? 4 : es) * (size_t)n;
+                if (b) s = h2d(dst[comp], (const char *)host_in + at, b);
+                at += b;
             }
-            at += esz * (size_t)n;
-        }
+        });
+        if (s != LPIC_OK) return s;
         c->dispatch([&](auto &S) { launch_finish_upload(S, (int)n, c->st); });
         c->np_upper = n;
         c->since_sort = 0;
