@@ -195,9 +195,12 @@ lpic_status lpic_diagnose(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, si
 /* Asynchronous form of lpic_diagnose for the on-axis wake (LPIC_DIAG_EX_AXIS, same layout:
  * Nx doubles): enqueues the read into host_out on the context stream and returns without
  * synchronising, so that a caller can consume step n's wake while step n+1 runs.  host_out
- * should be page-locked (a pageable destination makes the copy synchronous); it holds the
- * result once the stream has passed this call (an event recorded after it, or any
- * synchronising call) and must stay valid until then.  Errors: LPIC_EINVAL for another kind
+ * should be page-locked: if the device can address it (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor, 8-byte aligned) the kernel writes the wake into it directly, with no
+ * copy on the stream; other page-locked memory is filled by a copy from the staging area, and
+ * a pageable destination makes that copy synchronous.  host_out holds the result once the
+ * stream has passed this call (an event recorded after it, or any synchronising call) and must
+ * stay valid until then.  Errors: LPIC_EINVAL for another kind
  * or a NULL host_out, LPIC_EBUFSIZE if cap < Nx * 8; device-side errors of earlier steps are
  * reported by the next synchronising call. */
 lpic_status lpic_diagnose_async(lpic_ctx *ctx, lpic_diag_kind kind, void *host_out, size_t cap);

@@ -665,9 +665,24 @@ lpic_status lpic_diagnose_async(lpic_ctx *c, lpic_diag_kind kind, void *host_out
         return c->fail(LPIC_EINVAL, "lpic_diagnose_async: LPIC_DIAG_EX_AXIS into a non-NULL buffer only");
     const size_t n = (size_t)c->geo.nx * sizeof(double);
     if (cap < n) return c->fail(LPIC_EBUFSIZE, "output buffer too small");
-    // the staging area is reused only by later work on the same stream, after this copy
-    c->dispatch([&](auto &S) { launch_diag_ex_axis(S, (double *)c->stage, c->st); });
-    cudaError_t e = cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->st);
+    // Page-locked host memory the device can address: the kernel writes the wake into it
+    // directly (no copy on the stream between two steps).  Else through the staging area,
+    // which is reused only by later work on the same stream, after this copy.
+    cudaPointerAttributes pa{};
+    void *mapped = nullptr;
+    if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer && (uintptr_t)pa.devicePointer % 8 == 0)
+            mapped = pa.devicePointer;
+    } else {
+        (void)cudaGetLastError();   // not a CUDA-known pointer: pageable memory
+    }
+    cudaError_t e = cudaSuccess;
+    if (mapped) {
+        c->dispatch([&](auto &S) { launch_diag_ex_axis(S, (double *)mapped, c->st); });
+    } else {
+        c->dispatch([&](auto &S) { launch_diag_ex_axis(S, (double *)c->stage, c->st); });
+        e = cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->st);
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "lpic_diagnose_async");
 }
