@@ -695,6 +695,7 @@ def slab_leg(nslab: int = 2, steps: int = 100, settle_steps: int = 300):
     ev[0].record(sl.stream)
     sl.step(steps)
     ev[1].record(sl.stream)
+    torch.cuda.synchronize()           # the two timed regions must not overlap on the device
     ev[2].record(one.stream)
     one.step(steps)
     ev[3].record(one.stream)

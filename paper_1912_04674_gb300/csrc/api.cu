@@ -1028,8 +1028,13 @@ lpic_status lpic_slab_exchange(lpic_ctx *l, lpic_ctx *r, int32_t halo) {
     if (s == LPIC_OK) s = deferred_errors(r);
     if (s != LPIC_OK) return s;
     const int B_L = (int)(B - l->ph.x0);
-    if (l->prec == LPIC_FP64) launch_slab_exchange<double>(l->sd, r->sd, B_L, halo, l->st);
-    else launch_slab_exchange<float>(l->sf, r->sf, B_L, halo, l->st);
+    // the freed-slot lists live in each side's staging area (free between calls)
+    const size_t fb = l->stage_bytes < r->stage_bytes ? l->stage_bytes : r->stage_bytes;
+    const int fcap = (int)(fb / sizeof(int) < (size_t)(1 << 30) ? fb / sizeof(int) : (size_t)(1 << 30));
+    if (l->prec == LPIC_FP64)
+        launch_slab_exchange<double>(l->sd, r->sd, B_L, halo, (int *)l->stage, (int *)r->stage, fcap, l->st);
+    else
+        launch_slab_exchange<float>(l->sf, r->sf, B_L, halo, (int *)l->stage, (int *)r->stage, fcap, l->st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return l->cuda_fail(e, "lpic_slab_exchange");
     // appended electrons: the launch bounds and the next sort cover every slot

@@ -37,7 +37,9 @@ struct Desc {
     unsigned done;     // blocks of the window kernel finished this step (last one advances)
     int off_step;      // `off` as the step began (copied by the prepass): Ampere reads it while
                        // the window step, in the same launch, may already have advanced `off`
-    int pad[3];
+    int nfree;         // slab exchange: slots freed by its removal (listed in the staging area)
+    int ntaken;        // slab exchange: appended electrons so far (freed slots first)
+    int pad;
 };
 static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
 
@@ -329,9 +331,11 @@ template <class R> void launch_relocate(const SimDev<R> &S, int new_off, cudaStr
 
 // ---- x-slab exchange (slab.cu): halo columns of the persistent arrays from the owner, then
 // the electrons: remove those outside [lo, hi) (local cells) from each side and append the
-// other side's electrons in its halo cells.
+// other side's electrons in its halo cells, into the slots the removal freed first (freeL,
+// freeR: scratch for fcap slot indices per side).
 template <class R>
-void launch_slab_exchange(const SimDev<R> &L, const SimDev<R> &Rt, int B_L, int halo, cudaStream_t st);
+void launch_slab_exchange(const SimDev<R> &L, const SimDev<R> &Rt, int B_L, int halo, int *freeL, int *freeR,
+                          int fcap, cudaStream_t st);
 
 // ---- injected bunch: its charge from particle slots [k0, k0 + n), the discrete Gauss-law solve
 // (preconditioned CG to relative residual tol, at most max_iter iterations) and the addition of

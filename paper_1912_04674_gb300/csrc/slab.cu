@@ -45,27 +45,41 @@ template <class R> __global__ void k_slab_fields(SimDev<R> L, SimDev<R> Rt, int 
     }
 }
 
-// Remove the electrons whose local cell is outside [lo, hi).
-template <class R> __global__ void k_slab_keep(SimDev<R> S, int lo, int hi) {
+// Remove the electrons whose local cell is outside [lo, hi), and list the freed slots (up to
+// fcap of them, warp-aggregated) for the appends of the same exchange.
+template <class R> __global__ void k_slab_keep(SimDev<R> S, int lo, int hi, int *freed, int fcap) {
     const Parts<R> P = S.d->pbuf ? S.p[1] : S.p[0];
     const long long sh = S.d->shift;
     const int np = S.d->np;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
-        const int ix = P.ix[k];
-        if (ix == kDead) continue;
+    const int lane = threadIdx.x & 31;
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < np; base += gridDim.x * blockDim.x) {
+        const int k = base + lane;
+        const int ix = k < np ? P.ix[k] : kDead;
         const long long irel = (long long)ix - sh;
-        if (irel < lo || irel >= hi) P.ix[k] = kDead;
+        const bool drop = ix != kDead && (irel < lo || irel >= hi);
+        const unsigned m = __ballot_sync(FULL, drop);
+        if (!m) continue;
+        int first = 0;
+        if (lane == 0) first = atomicAdd(&S.d->nfree, __popc(m));
+        first = __shfl_sync(FULL, first, 0);
+        if (!drop) continue;
+        P.ix[k] = kDead;
+        const int t = first + __popc(m & ((1u << lane) - 1u));
+        if (t < fcap) freed[t] = k;
     }
 }
 
-// Append the source's electrons in its local cells [lo, hi) to the destination's slots from
-// its np on (warp-aggregated slot claims); slots beyond the capacity are not written and latch
-// ERR_CAPACITY (k_slab_clamp then trims np).
-template <class R> __global__ void k_slab_append(SimDev<R> Src, SimDev<R> Dst, int lo, int hi) {
+// Append the source's electrons in its local cells [lo, hi) to the destination: the slots its
+// removal freed first (they sit where the halo cells' electrons were sorted), then slots from
+// its np on (warp-aggregated claims).  Slots beyond the capacity are not written and latch
+// ERR_CAPACITY.
+template <class R> __global__ void k_slab_append(SimDev<R> Src, SimDev<R> Dst, int lo, int hi, const int *freed,
+                                                 int fcap) {
     const Parts<R> P = Src.d->pbuf ? Src.p[1] : Src.p[0];
     const Parts<R> Q = Dst.d->pbuf ? Dst.p[1] : Dst.p[0];
     const long long sh = Src.d->shift;
     const int np = Src.d->np, cap = Dst.ph.cap;
+    const int nfree = min(Dst.d->nfree, fcap), np0 = Dst.d->np;
     const int lane = threadIdx.x & 31;
     for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < np; base += gridDim.x * blockDim.x) {
         const int k = base + lane;
@@ -75,10 +89,11 @@ template <class R> __global__ void k_slab_append(SimDev<R> Src, SimDev<R> Dst, i
         const unsigned m = __ballot_sync(FULL, sel);
         if (!m) continue;
         int first = 0;
-        if (lane == 0) first = atomicAdd(&Dst.d->np, __popc(m));
+        if (lane == 0) first = atomicAdd(&Dst.d->ntaken, __popc(m));
         first = __shfl_sync(FULL, first, 0);
         if (!sel) continue;
-        const int slot = first + __popc(m & ((1u << lane) - 1u));
+        const int t = first + __popc(m & ((1u << lane) - 1u));
+        const long long slot = t < nfree ? (long long)freed[t] : (long long)np0 + (t - nfree);
         if (slot >= cap) {
             atomicOr(&Dst.d->err, (int)ERR_CAPACITY);
             continue;
@@ -95,8 +110,16 @@ template <class R> __global__ void k_slab_append(SimDev<R> Src, SimDev<R> Dst, i
     }
 }
 
-template <class R> __global__ void k_slab_clamp(SimDev<R> S) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && S.d->np > S.ph.cap) S.d->np = S.ph.cap;
+// np grows by the appends that found no freed slot (within the capacity); the counters are
+// zeroed for the next exchange.
+template <class R> __global__ void k_slab_settle(SimDev<R> S, int fcap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int nfree = min(S.d->nfree, fcap);
+        const long long grown = (long long)S.d->np + max(S.d->ntaken - nfree, 0);
+        S.d->np = (int)(grown < S.ph.cap ? grown : S.ph.cap);
+        S.d->nfree = 0;
+        S.d->ntaken = 0;
+    }
 }
 
 int blocks_for(long long n) {
@@ -106,21 +129,26 @@ int blocks_for(long long n) {
 
 }  // namespace
 
-// B_L: the boundary in the left slab's local columns.  Both slabs' np are read on the device,
-// so the particle kernels are sized for the capacities.
+// B_L: the boundary in the left slab's local columns; freeL / freeR: scratch for fcap slot
+// indices of each side (its staging area).  Both slabs' np are read on the device, so the
+// particle kernels are sized for the capacities.  The appends read np of the destination as
+// the keep left it: the destination's removal runs first, both removals before the appends.
 template <class R>
-void launch_slab_exchange(const SimDev<R> &L, const SimDev<R> &Rt, int B_L, int halo, cudaStream_t st) {
+void launch_slab_exchange(const SimDev<R> &L, const SimDev<R> &Rt, int B_L, int halo, int *freeL, int *freeR,
+                          int fcap, cudaStream_t st) {
     const long long cols = (long long)(halo + 1) * L.geo.P;
     k_slab_fields<R><<<dim3(blocks_for(cols), 10), TPB, 0, st>>>(L, Rt, B_L, halo);
-    k_slab_keep<R><<<blocks_for(L.ph.cap), TPB, 0, st>>>(L, -(1 << 30), B_L);
-    k_slab_keep<R><<<blocks_for(Rt.ph.cap), TPB, 0, st>>>(Rt, halo, 1 << 30);
-    k_slab_append<R><<<blocks_for(Rt.ph.cap), TPB, 0, st>>>(Rt, L, halo, 2 * halo);
-    k_slab_append<R><<<blocks_for(L.ph.cap), TPB, 0, st>>>(L, Rt, B_L - halo, B_L);
-    k_slab_clamp<R><<<1, 32, 0, st>>>(L);
-    k_slab_clamp<R><<<1, 32, 0, st>>>(Rt);
+    k_slab_keep<R><<<blocks_for(L.ph.cap), TPB, 0, st>>>(L, -(1 << 30), B_L, freeL, fcap);
+    k_slab_keep<R><<<blocks_for(Rt.ph.cap), TPB, 0, st>>>(Rt, halo, 1 << 30, freeR, fcap);
+    k_slab_append<R><<<blocks_for(Rt.ph.cap), TPB, 0, st>>>(Rt, L, halo, 2 * halo, freeL, fcap);
+    k_slab_append<R><<<blocks_for(L.ph.cap), TPB, 0, st>>>(L, Rt, B_L - halo, B_L, freeR, fcap);
+    k_slab_settle<R><<<1, 32, 0, st>>>(L, fcap);
+    k_slab_settle<R><<<1, 32, 0, st>>>(Rt, fcap);
 }
 
-template void launch_slab_exchange<double>(const SimDev<double> &, const SimDev<double> &, int, int, cudaStream_t);
-template void launch_slab_exchange<float>(const SimDev<float> &, const SimDev<float> &, int, int, cudaStream_t);
+template void launch_slab_exchange<double>(const SimDev<double> &, const SimDev<double> &, int, int, int *, int *,
+                                           int, cudaStream_t);
+template void launch_slab_exchange<float>(const SimDev<float> &, const SimDev<float> &, int, int, int *, int *, int,
+                                          cudaStream_t);
 
 }  // namespace lpic
