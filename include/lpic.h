@@ -264,9 +264,10 @@ lpic_status lpic_envelope_stats_noalloc(const void *a_dev, int32_t nx, int32_t n
  * right the cells from B on.  After both have completed the same step, this call enqueues:
  *   - E, B_theta, A^n and A^{n-1} of the owner copied into the other's halo columns (right's
  *     nodes [B, B+halo] and cells [B, B+halo) into left; left's [B-halo, B) into right);
- *   - left's electrons in cells >= B and right's in cells < B removed (holes until the next
- *     sort), then right's electrons in cells [B, B+halo) appended to left and left's in
- *     [B-halo, B) appended to right (same ids: the owner keeps its own),
+ *   - left's electrons in cells >= B and right's in cells < B removed, then right's
+ *     electrons in cells [B, B+halo) appended to left and left's in [B-halo, B) appended to
+ *     right (same ids: the owner keeps its own), each into the slots its removal freed first
+ *     (listed in the context's staging area) and then past its slots in use,
  * so that each slab computes its owned columns of the next step exactly as one whole window
  * would: one step's phases reach at most 6 columns from a wrong boundary value (Faraday,
  * gather, deposit, envelope, position push, current, Ampere and the window shift), so halo >= 8
