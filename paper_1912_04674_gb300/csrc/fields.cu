@@ -49,26 +49,28 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
     }
     S.f.btn[id] = btn_here;
     if constexpr (sizeof(R) == 4) {
-        // radial pairs for the FP32 gathers (nodes i in [-1, nx+1], j in [-1, nr]).  E is not
-        // written by this kernel outside column -1, so a thread reads its upper neighbour; the
-        // column -1, which this kernel zeroes, gets zero pairs without reading it.  B is updated
-        // in place, so B^n of node (i, j) is stored by its own thread into both records that
-        // hold it: (i, j).x and (i, j-1).y (separate 4-byte words, no two threads write the
-        // same one).
+        // x-pairs for the FP32 gathers, record (i, j) = (F(i, j), F(i+1, j)) for nodes i in
+        // [-1, nx+1], j in [-1, nr+1].  E is not written by this kernel outside column -1 (whose
+        // values are zero: its own thread knows them), so a thread reads its right neighbour.
+        // B is updated in place, so B^n of node (i, j) is stored by its own thread into both
+        // records that hold it: (i, j).x and (i-1, j).y (separate 4-byte words, no two threads
+        // write the same one).  Row -1 holds the odd mirror, the negated row 0 (read for Er and
+        // Btheta only).
         if (i >= -1 && i <= g.nx + 1 && j <= g.nr + 1) {
             float *bq = reinterpret_cast<float *>(S.f.btq);
+            const long long P = g.P;
             bq[2 * (long long)id] = btn_here;
-            bq[2 * (long long)id - 1] = btn_here;   // (i, j-1).y; for j = 0 that of row -1
-            if (j <= g.nr) {
-                const bool guard = i == -1;
-                const R ex0 = guard ? (R)0 : S.f.ex[id], er0 = guard ? (R)0 : S.f.er[id];
-                S.f.exq[id] = make_float2(ex0, guard ? (R)0 : S.f.ex[id + 1]);
-                S.f.erq[id] = make_float2(er0, guard ? (R)0 : S.f.er[id + 1]);
-                if (j == 0) {   // row -1: the odd mirror (read for Er and Btheta only)
-                    S.f.exq[id - 1] = make_float2(-ex0, ex0);
-                    S.f.erq[id - 1] = make_float2(-er0, er0);
-                    bq[2 * (long long)id - 2] = -btn_here;
-                }
+            if (i >= 0) bq[2 * ((long long)id - P) + 1] = btn_here;   // (i-1, j).y (column -2 unread)
+            const bool guard = i == -1;
+            const R ex0 = guard ? (R)0 : S.f.ex[id], er0 = guard ? (R)0 : S.f.er[id];
+            const R ex1 = S.f.ex[id + P], er1 = S.f.er[id + P];
+            S.f.exq[id] = make_float2(ex0, ex1);
+            S.f.erq[id] = make_float2(er0, er1);
+            if (j == 0) {
+                S.f.exq[id - 1] = make_float2(-ex0, -ex1);
+                S.f.erq[id - 1] = make_float2(-er0, -er1);
+                bq[2 * ((long long)id - 1)] = -btn_here;                          // (i, -1).x
+                if (i >= 0) bq[2 * ((long long)id - 1 - P) + 1] = -btn_here;      // (i-1, -1).y
             }
         }
     }

@@ -68,10 +68,10 @@ template <class R> struct Fields {
     typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
     R *btn, *phih;                   // per step: B^n, Phi^{n+1/2}
     Q4<R> *pg;                       // per step: (Phi^n, dPhi/dx, dPhi/dr)
-    // per step, FP32 contexts only (else null): E^n and B^n as pairs of radial neighbours,
-    // element (i, j) = (F(i, j), F(i, j+1)), so that a gather reads two 8-byte records; the
-    // element of row -1 (the spare last row of the previous column) is (-F(i, 0), F(i, 0)),
-    // the odd mirror of Er and Btheta across the axis
+    // per step, FP32 contexts only (else null): E^n and B^n as pairs of x neighbours,
+    // element (i, j) = (F(i, j), F(i+1, j)), so that a gather reads two adjacent 8-byte
+    // records; the element of row -1 (the spare last row of the previous column) is
+    // (-F(i, 0), -F(i+1, 0)), the odd mirror of Er and Btheta across the axis
     typename Cplx<R>::t *exq, *erq, *btq;
     double *chi, *jx, *jr, *dq;      // per step FP64 accumulators (deposit targets), before
                                      // their row factors (RowTab): chi sum w S/gamma, Jx and

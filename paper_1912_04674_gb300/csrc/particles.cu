@@ -195,13 +195,14 @@ __device__ __forceinline__ int2 slot_range(int np, int vb, int nvb, int csize) {
     return make_int2(begin, min(begin + chunk, np));
 }
 
-// Gather from radial pairs (FP32 pass A): the same weights and the same sum as gather4, with
-// the two rows of a column in one 8-byte record; row -1 holds the odd mirror.
+// Gather from x-pairs (FP32 pass A): the same weights and the same sum as gather4, with the
+// two columns of a row in one 8-byte record and the next row in the next record (an immediate
+// offset from the first); row -1 holds the odd mirror.
 __device__ __forceinline__ float gather_q(const float2 *__restrict__ G, const Geo &geo, int off, int i, float f,
                                           int j, float gw) {
-    const int b = geo.at(off, i, j);
-    const float2 c0 = __ldg(G + b), c1 = __ldg(G + b + geo.P);
-    const float lo = c0.x + f * (c1.x - c0.x), hi = c0.y + f * (c1.y - c0.y);
+    const float2 *r = G + geo.at(off, i, j);
+    const float2 c0 = __ldg(r), c1 = __ldg(r + 1);
+    const float lo = c0.x + f * (c0.y - c0.x), hi = c1.x + f * (c1.y - c1.x);
     return lo + gw * (hi - lo);
 }
 
