@@ -47,7 +47,7 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
         S.f.bt[id] = bnew;
         btn_here = (R)0.5 * (bold + bnew);
     }
-    S.f.btn[id] = btn_here;
+    if constexpr (sizeof(R) == 8) S.f.btn[id] = btn_here;   // FP32 gathers read the x-pairs below
     if constexpr (sizeof(R) == 4) {
         // x-pairs for the FP32 gathers, record (i, j) = (F(i, j), F(i+1, j)) for nodes i in
         // [-1, nx+1], j in [-1, nr+1].  E is not written by this kernel outside column -1 (whose

@@ -66,7 +66,7 @@ template <class R> struct alignas(4 * sizeof(R)) Q4 {
 template <class R> struct Fields {
     R *ex, *er, *bt;                 // persistent: E^n, B^{n-1/2} -> B^{n+1/2}
     typename Cplx<R>::t *a[2];       // persistent: A^n = a[abuf], A^{n-1} = a[abuf^1]
-    R *btn, *phih;                   // per step: B^n, Phi^{n+1/2}
+    R *btn, *phih;                   // per step: B^n (FP64 contexts; FP32 reads btq), Phi^{n+1/2}
     Q4<R> *pg;                       // per step: (Phi^n, dPhi/dx, dPhi/dr)
     // per step, FP32 contexts only (else null): E^n and B^n as pairs of x neighbours,
     // element (i, j) = (F(i, j), F(i+1, j)), so that a gather reads two adjacent 8-byte

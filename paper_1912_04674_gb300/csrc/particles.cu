@@ -510,20 +510,37 @@ __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const flo
                                              const float (&bnd)[M], int ba, int bb, double *const (&base)[4],
                                              const int (&o)[4]) {
     const int lane = threadIdx.x & 31;
-    int qa[4], qb[4], ec[M];
-    bool bad[M];
+    int ec[M];
+    float sc[M];
+    bool bad[M], anybad = false;
 #pragma unroll
     for (int m = 0; m < M; m++) {
         const unsigned e = ((unsigned)__float_as_uint(bnd[m]) >> 23) & 0xffu;
         const int emax = (int)__reduce_max_sync(FULL, e);
         bad[m] = emax == 255;
+        anybad |= bad[m];
         ec[m] = min(max(emax, 25), 254);
-        const float sc = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
+        sc[m] = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
+    }
+    if (anybad) {   // warp-uniform, rare: every element deposits alone, NaN in a bad group
 #pragma unroll
-        for (int q = m * 4 / M; q < (m + 1) * 4 / M; q++) {
-            qa[q] = bad[m] ? 0 : __float2int_rn(va[q] * sc);
-            qb[q] = bad[m] ? 0 : __float2int_rn(vb[q] * sc);
+        for (int q = 0; q < 4; q++) {
+            const int m = q * M / 4;
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            const int qa = bad[m] ? 0 : __float2int_rn(va[q] * sc[m]);
+            const int qb = bad[m] ? 0 : __float2int_rn(vb[q] * sc[m]);
+            if (ka != kNoKey && (bad[m] || qa != 0))
+                atomicAdd(base[q] + ba + o[q], bad[m] ? nan : scaled_int_to_double(qa, ec[m] + 1));
+            if (kb != kNoKey && (bad[m] || qb != 0))
+                atomicAdd(base[q] + bb + o[q], bad[m] ? nan : scaled_int_to_double(qb, ec[m] + 1));
         }
+        return;
+    }
+    int qa[4], qb[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        qa[q] = __float2int_rn(va[q] * sc[q * M / 4]);
+        qb[q] = __float2int_rn(vb[q] * sc[q * M / 4]);
     }
     const bool fold = ka == kb;              // a joins b (also when both are holes)
 #pragma unroll
@@ -558,14 +575,8 @@ __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const flo
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         const int m = q * M / 4;
-        if (dep_a) {
-            if (bad[m]) atomicAdd(base[q] + ba + o[q], __longlong_as_double(0x7ff8000000000000ll));
-            else if (qa[q] != 0) atomicAdd(base[q] + ba + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
-        }
-        if (dep_b) {
-            if (bad[m]) atomicAdd(base[q] + bb + o[q], __longlong_as_double(0x7ff8000000000000ll));
-            else if (qb[q] != 0) atomicAdd(base[q] + bb + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
-        }
+        if (dep_a && qa[q] != 0) atomicAdd(base[q] + ba + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
+        if (dep_b && qb[q] != 0) atomicAdd(base[q] + bb + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
     }
 }
 
@@ -583,7 +594,8 @@ __device__ __forceinline__ void bucket_deposit(int4 *bk, unsigned ka, unsigned k
                                                const float (&vb)[4], const float (&bnd)[M], int ba, int bb,
                                                double *const (&base)[4], const int (&o)[4]) {
     const int lane = threadIdx.x & 31;
-    int qa[4], qb[4], ec[M];
+    int ec[M];
+    float sc[M];
     bool bad[M], anybad = false;
 #pragma unroll
     for (int m = 0; m < M; m++) {
@@ -592,24 +604,27 @@ __device__ __forceinline__ void bucket_deposit(int4 *bk, unsigned ka, unsigned k
         bad[m] = emax == 255;
         anybad |= bad[m];
         ec[m] = min(max(emax, 25), 254);
-        const float sc = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
-#pragma unroll
-        for (int q = m * 4 / M; q < (m + 1) * 4 / M; q++) {
-            qa[q] = bad[m] ? 0 : __float2int_rn(va[q] * sc);
-            qb[q] = bad[m] ? 0 : __float2int_rn(vb[q] * sc);
-        }
+        sc[m] = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
     }
-    if (anybad) {   // warp-uniform
+    if (anybad) {   // warp-uniform, rare: every element deposits alone
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int m = q * M / 4;
             const double nan = __longlong_as_double(0x7ff8000000000000ll);
-            if (ka != kNoKey && (bad[m] || qa[q] != 0))
-                atomicAdd(base[q] + ba + o[q], bad[m] ? nan : scaled_int_to_double(qa[q], ec[m] + 1));
-            if (kb != kNoKey && (bad[m] || qb[q] != 0))
-                atomicAdd(base[q] + bb + o[q], bad[m] ? nan : scaled_int_to_double(qb[q], ec[m] + 1));
+            const int qa = bad[m] ? 0 : __float2int_rn(va[q] * sc[m]);
+            const int qb = bad[m] ? 0 : __float2int_rn(vb[q] * sc[m]);
+            if (ka != kNoKey && (bad[m] || qa != 0))
+                atomicAdd(base[q] + ba + o[q], bad[m] ? nan : scaled_int_to_double(qa, ec[m] + 1));
+            if (kb != kNoKey && (bad[m] || qb != 0))
+                atomicAdd(base[q] + bb + o[q], bad[m] ? nan : scaled_int_to_double(qb, ec[m] + 1));
         }
         return;
+    }
+    int qa[4], qb[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        qa[q] = __float2int_rn(va[q] * sc[q * M / 4]);
+        qb[q] = __float2int_rn(vb[q] * sc[q * M / 4]);
     }
     if (ka == kb) {   // a joins b (also when both are holes)
 #pragma unroll
@@ -634,7 +649,7 @@ __device__ __forceinline__ void bucket_deposit(int4 *bk, unsigned ka, unsigned k
         const int b = (int)(k0 + (unsigned)lane);
         const int sv[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < 4; q++)   // (scaled_int_to_double is defined for q != 0 only)
             if (sv[q] != 0) atomicAdd(base[q] + b + o[q], scaled_int_to_double(sv[q], ec[q * M / 4] + 1));
     }
     __syncwarp();
