@@ -338,9 +338,9 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
 // fewer load, reduction and atomic instructions per particle.)  The push of the pair runs in
 // packed FP32x2 arithmetic (a_pair, b_pair): 30 fewer thread instructions per particle in
 // pass A (292 -> 262) and 15 in pass B, 4-6 % off each pass.  Pass A deposits through the
-// warp's shared-memory buckets instead (bucket_deposit: 262 -> 232 instructions per particle,
-// 4 % off pass A); in pass B the buckets cut instructions as well but the pass ran 2 % slower
-// (its crossing queue already holds most of the block's shared memory), so it keeps the runs.
+// warp's shared-memory node buckets instead (node_bucket_deposit: per-cell buckets took pass A
+// from 0.105 to 0.101 ms, per-node ones to 0.093 ms); in pass B per-cell buckets cut
+// instructions as well but the pass ran 2 % slower, so it keeps the runs.
 
 // The position half of a pair (carried one iteration ahead) and the rest (loaded at the top
 // of the iteration that uses it).  Particle data is read and written once per pass: it goes
@@ -580,51 +580,40 @@ __device__ __forceinline__ void pair_deposit(unsigned ka, unsigned kb, const flo
     }
 }
 
-// Deposit of a warp's 64 elements through warp-private buckets in shared memory: bucket c
-// holds the four integer sums of the elements whose cell key is k0 + c (k0 the warp's lowest
-// key, c < NBK).  Values are scaled as in pair_deposit (group m of a value q*M/4, one scale
-// per warp and group, 64 values per warp: exact in 32-bit integers); each element adds its four
-// integers with shared-memory atomics, then lane c turns bucket c's sums into FP64 exactly and
-// adds them to the nodes of cell k0 + c, and zeroes the bucket.  Elements whose key lies
-// outside the 32 cells (far from their sorted place) add their values alone.  A non-finite
-// value in the warp makes its group's deposits NaN (all of the warp's elements deposit alone).
-constexpr int NBK = 32;
-template <int M>
-__device__ __forceinline__ void bucket_deposit(int4 *bk, unsigned ka, unsigned kb, const float (&va)[4],
-                                               const float (&vb)[4], const float (&bnd)[M], int ba, int bb,
-                                               double *const (&base)[4], const int (&o)[4]) {
+// chi deposit of a warp's 64 elements through warp-private node buckets in shared memory:
+// seg0[r] sums the values of node k0 + r, seg1[r] those of node k0 + P + r (k0 the warp's
+// lowest cell key; an element of cell k0 + r adds w00 to seg0[r], w01 to seg0[r+1], w10 to
+// seg1[r], w11 to seg1[r+1]), so that a node shared by neighbouring cells takes one
+// reduction.  Sorted keys are consecutive within a column and jump by P - Nr + 1 between
+// columns, so a warp's elements (about 4 cells) fit in the 31 cells from k0.  Values are
+// scaled as in pair_deposit (one scale per warp, 64 values: exact in 32-bit integers); each
+// element adds its four integers with shared-memory atomics, then lane r turns seg0[r] and
+// seg1[r] into FP64 exactly, adds them to their nodes and zeroes them.  Elements outside the
+// 31 cells (far from their sorted place) add their values alone; a non-finite value in the
+// warp makes its deposits NaN.
+__device__ __forceinline__ void node_bucket_deposit(int *seg, unsigned ka, unsigned kb, const float (&va)[4],
+                                                    const float (&vb)[4], float bnd, int ba, int bb, double *chi,
+                                                    int P) {
     const int lane = threadIdx.x & 31;
-    int ec[M];
-    float sc[M];
-    bool bad[M], anybad = false;
-#pragma unroll
-    for (int m = 0; m < M; m++) {
-        const unsigned e = ((unsigned)__float_as_uint(bnd[m]) >> 23) & 0xffu;
-        const int emax = (int)__reduce_max_sync(FULL, e);
-        bad[m] = emax == 255;
-        anybad |= bad[m];
-        ec[m] = min(max(emax, 25), 254);
-        sc[m] = __uint_as_float((unsigned)(277 - ec[m]) << 23);   // 2^(150 - ec)
-    }
-    if (anybad) {   // warp-uniform, rare: every element deposits alone
+    const unsigned e = ((unsigned)__float_as_uint(bnd) >> 23) & 0xffu;
+    const int emax = (int)__reduce_max_sync(FULL, e);
+    const int ec = min(max(emax, 25), 254);
+    const float sc = __uint_as_float((unsigned)(277 - ec) << 23);   // 2^(150 - ec)
+    const int o[4] = {0, P, 1, P + 1};
+    if (emax == 255) {   // warp-uniform, rare: every element deposits NaN
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int m = q * M / 4;
-            const double nan = __longlong_as_double(0x7ff8000000000000ll);
-            const int qa = bad[m] ? 0 : __float2int_rn(va[q] * sc[m]);
-            const int qb = bad[m] ? 0 : __float2int_rn(vb[q] * sc[m]);
-            if (ka != kNoKey && (bad[m] || qa != 0))
-                atomicAdd(base[q] + ba + o[q], bad[m] ? nan : scaled_int_to_double(qa, ec[m] + 1));
-            if (kb != kNoKey && (bad[m] || qb != 0))
-                atomicAdd(base[q] + bb + o[q], bad[m] ? nan : scaled_int_to_double(qb, ec[m] + 1));
+            if (ka != kNoKey) atomicAdd(chi + ba + o[q], nan);
+            if (kb != kNoKey) atomicAdd(chi + bb + o[q], nan);
         }
         return;
     }
     int qa[4], qb[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        qa[q] = __float2int_rn(va[q] * sc[q * M / 4]);
-        qb[q] = __float2int_rn(vb[q] * sc[q * M / 4]);
+        qa[q] = __float2int_rn(va[q] * sc);
+        qb[q] = __float2int_rn(vb[q] * sc);
     }
     if (ka == kb) {   // a joins b (also when both are holes)
 #pragma unroll
@@ -632,34 +621,35 @@ __device__ __forceinline__ void bucket_deposit(int4 *bk, unsigned ka, unsigned k
         ka = kNoKey;
     }
     const unsigned k0 = __reduce_min_sync(FULL, min(ka, kb));
-    const bool ina = ka != kNoKey && ka - k0 < (unsigned)NBK;
-    const bool inb = kb != kNoKey && kb - k0 < (unsigned)NBK;
+    const bool ina = ka != kNoKey && ka - k0 < 31u;
+    const bool inb = kb != kNoKey && kb - k0 < 31u;
+    int *const s0 = seg, *const s1 = seg + 32;
     if (ina) {
-        int *c = &bk[ka - k0].x;
-        atomicAdd(c, qa[0]); atomicAdd(c + 1, qa[1]); atomicAdd(c + 2, qa[2]); atomicAdd(c + 3, qa[3]);
+        const int r = (int)(ka - k0);
+        atomicAdd(s0 + r, qa[0]); atomicAdd(s0 + r + 1, qa[2]); atomicAdd(s1 + r, qa[1]); atomicAdd(s1 + r + 1, qa[3]);
     }
     if (inb) {
-        int *c = &bk[kb - k0].x;
-        atomicAdd(c, qb[0]); atomicAdd(c + 1, qb[1]); atomicAdd(c + 2, qb[2]); atomicAdd(c + 3, qb[3]);
+        const int r = (int)(kb - k0);
+        atomicAdd(s0 + r, qb[0]); atomicAdd(s0 + r + 1, qb[2]); atomicAdd(s1 + r, qb[1]); atomicAdd(s1 + r + 1, qb[3]);
     }
     __syncwarp();
-    const int4 s = bk[lane];
-    if (s.x | s.y | s.z | s.w) {
-        bk[lane] = make_int4(0, 0, 0, 0);
-        const int b = (int)(k0 + (unsigned)lane);
-        const int sv[4] = {s.x, s.y, s.z, s.w};
-#pragma unroll
-        for (int q = 0; q < 4; q++)   // (scaled_int_to_double is defined for q != 0 only)
-            if (sv[q] != 0) atomicAdd(base[q] + b + o[q], scaled_int_to_double(sv[q], ec[q * M / 4] + 1));
+    const int v0 = s0[lane], v1 = s1[lane];
+    const int n0 = (int)(k0 + (unsigned)lane);
+    if (v0 != 0) {   // (scaled_int_to_double is defined for q != 0 only)
+        s0[lane] = 0;
+        atomicAdd(chi + n0, scaled_int_to_double(v0, ec + 1));
+    }
+    if (v1 != 0) {
+        s1[lane] = 0;
+        atomicAdd(chi + n0 + P, scaled_int_to_double(v1, ec + 1));
     }
     __syncwarp();
     const bool oa = ka != kNoKey && !ina, ob = kb != kNoKey && !inb;
     if (__any_sync(FULL, oa || ob)) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int m = q * M / 4;
-            if (oa && qa[q] != 0) atomicAdd(base[q] + ba + o[q], scaled_int_to_double(qa[q], ec[m] + 1));
-            if (ob && qb[q] != 0) atomicAdd(base[q] + bb + o[q], scaled_int_to_double(qb[q], ec[m] + 1));
+            if (oa && qa[q] != 0) atomicAdd(chi + ba + o[q], scaled_int_to_double(qa[q], ec + 1));
+            if (ob && qb[q] != 0) atomicAdd(chi + bb + o[q], scaled_int_to_double(qb[q], ec + 1));
         }
     }
 }
@@ -671,9 +661,10 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
     const long long shift = S.d->shift;
     const int2 rg = slot_range(np, vb, nvb, csize);   // begin is even: chunks are multiples of TPB
     const int begin = rg.x, end = rg.y;
-    __shared__ int4 buckets[TPB / 32][NBK];
-    int4 *bk = buckets[threadIdx.x >> 5];
-    bk[threadIdx.x & 31] = make_int4(0, 0, 0, 0);
+    __shared__ int segs[TPB / 32][64];
+    int *seg = segs[threadIdx.x >> 5];
+    seg[threadIdx.x & 31] = 0;
+    seg[32 + (threadIdx.x & 31)] = 0;
     __syncwarp();
     int k = begin + 2 * threadIdx.x;
     PPos cur = load_pos(P, k, end);
@@ -693,10 +684,7 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
             if (la) { __stcs(P.px + k, a.px); __stcs(P.py + k, a.py); __stcs(P.pz + k, a.pz); }
             if (lb) { __stcs(P.px + k + 1, b.px); __stcs(P.py + k + 1, b.py); __stcs(P.pz + k + 1, b.pz); }
         }
-        const float bnd[1] = {a.bnd > b.bnd ? a.bnd : b.bnd};
-        double *const base_q[4] = {S.f.chi, S.f.chi, S.f.chi, S.f.chi};
-        const int o[4] = {0, geo.P, 1, geo.P + 1};
-        bucket_deposit<1>(bk, a.key, b.key, a.v, b.v, bnd, a.b, b.b, base_q, o);
+        node_bucket_deposit(seg, a.key, b.key, a.v, b.v, a.bnd > b.bnd ? a.bnd : b.bnd, a.b, b.b, S.f.chi, geo.P);
         cur = nxt;
     }
 }

@@ -1,9 +1,9 @@
 """The deposits do not depend on the order of the particles in memory.
 
-The passes sum each warp's deposits per cell before the FP64 atomics: FP32 pass A through
-warp-private buckets covering the 32 cells from the warp's lowest cell, FP32 pass B and the
-FP64 passes over runs of neighbouring lanes with equal cells.  Electrons outside a warp's 32
-cells deposit alone.  With the particle order shuffled at random (and a sort cadence longer
+The passes sum each warp's deposits per cell or node before the FP64 atomics: FP32 pass A
+through warp-private node buckets covering the 31 cells from the warp's lowest cell, FP32 pass
+B and the FP64 passes over runs of neighbouring lanes with equal cells.  Electrons outside a
+warp's 31 cells deposit alone.  With the particle order shuffled at random (and a sort cadence longer
 than the test, so that it stays shuffled) nearly every warp takes those single-electron paths.
 Bars, for two steps from an oracle state: FP64 against the oracle at 1e-10, as for a sorted
 state; FP32 shuffled and sorted against the oracle at the 1e-3 element-by-element bar of the
