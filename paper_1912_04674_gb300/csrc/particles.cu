@@ -994,7 +994,8 @@ __device__ __forceinline__ void b_pair(const SimDev<float> &S, const Geo &geo, i
 // FP32: two neighbouring particles per thread, as in pass A, pushed together in packed FP32x2
 // arithmetic (b_pair; 6 % faster than one particle after the other); the crossing moves of both
 // join the queue, which is drained at one place per iteration (one inlined copy of the general
-// deposit, not two).
+// deposit, not two).  Unlike pass A, the momenta are carried one iteration ahead too: they fit
+// in 64 registers here (8 blocks of 128 per SM instead of 9 at 56 registers; 1.7 % faster).
 template <>
 __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S, int vb, int nvb, int csize) {
     __shared__ CrossQueue<float> Q;
@@ -1009,9 +1010,11 @@ __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S
     const int begin = rg.x, end = rg.y;
     int k = begin + 2 * threadIdx.x;
     PPos cur = load_pos(P, k, end);
+    PMom mcur = load_mom(P, k, end);
     for (int base = begin; base < end; base += 2 * TPB_B, k += 2 * TPB_B) {
-        const PMom m = load_mom(P, k, end);
+        const PMom m = mcur;
         const PPos nxt = load_pos(P, k + 2 * TPB_B, end);   // prefetch
+        mcur = load_mom(P, k + 2 * TPB_B, end);
         BOut<float> a, b;
         b_pair(S, geo, off, shift, snext, cur, m, a, b);
         enqueue_cross<float>(Q, wq, queued, a, m.w.x);
