@@ -243,10 +243,11 @@ struct lpic_ctx {
         err = std::string(where) + ": " + cudaGetErrorString(e);
         return LPIC_ECUDA;
     }
-    // one step (and one step followed by the sort) recorded as CUDA graphs, replayed while
-    // kernel timing is off; launches per replay by family
-    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
-    long long step_launches[2][9] = {};
+    // one step, one step followed by the sort, and kMultiSteps steps without a sort, recorded
+    // as CUDA graphs and replayed while kernel timing is off; launches per replay by family
+    static constexpr int kMultiSteps = 8;
+    cudaGraphExec_t step_exec[3] = {nullptr, nullptr, nullptr};
+    long long step_launches[3][9] = {};
     void drop_step_graphs() {
         for (auto &e : step_exec)
             if (e) { cudaGraphExecDestroy(e); e = nullptr; }
@@ -611,7 +612,8 @@ lpic_status lpic_load_plasma(lpic_ctx *c, const lpic_plasma_params *p) {
 // Record one step (with_sort: followed by the counting sort) as a CUDA graph.  The particle
 // kernels are sized for the whole capacity (they read the live count from the device), so the
 // graph stays valid while the particle count changes.
-lpic_status capture_step(lpic_ctx *c, int with_sort) {
+// mode 0: one step; 1: one step and the sort; 2: kMultiSteps steps (no sort, no relocation)
+lpic_status capture_step(lpic_ctx *c, int mode) {
     static_assert(lpic_ctx::kFamilies == 9, "step_launches is sized for the kernel families");
     long long before[lpic_ctx::kFamilies];
     memcpy(before, c->launches, sizeof before);
@@ -620,15 +622,15 @@ lpic_status capture_step(lpic_ctx *c, int with_sort) {
     if (e != cudaSuccess) return c->cuda_fail(e, "step capture");
     const int npl = (int)c->g.particle_capacity, inj = inj_upper(c);
     c->dispatch([&](auto &S) {
-        enqueue_step_kernels(c, S, npl, inj, c->st);
-        if (with_sort)
+        for (int g = 0; g < (mode == 2 ? lpic_ctx::kMultiSteps : 1); g++) enqueue_step_kernels(c, S, npl, inj, c->st);
+        if (mode == 1)
             traced(c, F_SORT, kSortLaunches, c->st, [&] { launch_sort(S, npl, c->key, c->count, c->blocksum, c->st); });
     });
     e = cudaStreamEndCapture(c->st, &graph);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec[with_sort], graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec[mode], graph, 0);
     if (graph) cudaGraphDestroy(graph);
     for (int f = 0; f < lpic_ctx::kFamilies; f++) {
-        c->step_launches[with_sort][f] = c->launches[f] - before[f];
+        c->step_launches[mode][f] = c->launches[f] - before[f];
         c->launches[f] = before[f];
     }
     return e == cudaSuccess ? LPIC_OK : c->cuda_fail(e, "step graph");
@@ -640,6 +642,19 @@ lpic_status lpic_step(lpic_ctx *c, int nsteps) {
     lpic_status s = deferred_errors(c);
     if (s != LPIC_OK) return s;
     for (int k = 0; k < nsteps; k++) {
+        // kMultiSteps steps in one replay when none of them sorts or relocates (the window
+        // slides the offset by at most one column a step)
+        const int G = lpic_ctx::kMultiSteps;
+        if (!c->timing && nsteps - k >= G && c->since_sort + G < c->g.sort_every &&
+            (!c->g.moving_window || c->off + G + c->geo.nlive + 1 <= c->geo.ncol)) {
+            for (int g = 0; g < G; g++) (void)advance_mirror(c);   // no sort: since_sort stays below
+            if (!c->step_exec[2] && (s = capture_step(c, 2)) != LPIC_OK) return s;
+            cudaError_t e = cudaGraphLaunch(c->step_exec[2], c->st);
+            if (e != cudaSuccess) return c->cuda_fail(e, "lpic_step");
+            for (int f = 0; f < lpic_ctx::kFamilies; f++) c->launches[f] += c->step_launches[2][f];
+            k += G - 1;
+            continue;
+        }
         pre_step(c, c->st);
         if (c->timing) {   // kernel by kernel, bracketed with events
             const int npl = launch_cap(c), inj = inj_upper(c);
