@@ -26,7 +26,10 @@ template <class R> __device__ __forceinline__ void prepass_tile(const SimDev<R> 
     const int off = S.d->off;
     const int j = bx * BX + threadIdx.x;
     const int i = by * BY + (int)threadIdx.y - kG;
-    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) S.d->off_step = off;
+    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        S.d->off_step = off;
+        S.d->ticket = 0;   // for pass A
+    }
     if (j >= g.P || i > g.nx + kG) return;
     const long long id = g.at(off, i, j);
     const R dt = S.k.dt, idx_ = S.k.idx, idr = S.k.idr;
@@ -175,6 +178,7 @@ __device__ __forceinline__ void envelope_tile(const SimDev<R> &S, int bx, int by
 }
 
 template <class R> __global__ void k_envelope(SimDev<R> S) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) S.d->ticket = 0;   // for pass B
     envelope_tile<R>(S, blockIdx.x, blockIdx.y, blockIdx.x == gridDim.x - 1);
 }
 

@@ -39,7 +39,7 @@ struct Desc {
                        // the window step, in the same launch, may already have advanced `off`
     int nfree;         // slab exchange: slots freed by its removal (listed in the staging area)
     int ntaken;        // slab exchange: appended electrons so far (freed slots first)
-    int pad;
+    int ticket;        // units handed out by the FP32 particle passes (zeroed by the kernel before)
 };
 static_assert(sizeof(Desc) == 64, "Desc is one 64-byte line");
 
