@@ -180,19 +180,24 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
 }
 
 // Work split of the single-simulation FP32 passes: each block first takes a contiguous share
-// of 7/8 of the slots, in units of U slots (one iteration of the block), then single units of
-// the rest from the descriptor's ticket counter (zeroed by the kernel before), so that the
+// of num/den of the slots, in units of U slots (one iteration of the block), then single units
+// of the rest from the descriptor's ticket counter (zeroed by the kernel before), so that the
 // blocks of the SMs that finish their share early take more of the end.  With equal shares
 // only, the SMs' active cycles spread by 5-7 % of the launch (ncu sm__cycles_active min, avg,
-// max) and the launch lasted as long as the slowest; measured 3 % faster in each pass.
+// max) and the launch lasted as long as the slowest.  Measured (3 alternating runs each): pass
+// A 0.0923 ms with equal shares, 0.0896 at 7/8, 0.0883 at 15/16, 0.092 at 3/4, 0.098 at 1/2;
+// pass B 0.0925, 0.0905 at 7/8, 0.0945 at 15/16, 0.0915 at 3/4.  Each unit handed out costs
+// the ticket's round trip with the block waiting at a barrier; claiming the next unit one
+// iteration ahead (hiding that round trip) measured slower in pass B (spills) and within 0.5 %
+// in pass A.
 struct Split {
     int sbeg, send;   // the block's contiguous share
     int dyn0, nunits; // first unit handed out by ticket, number of units
 };
-__device__ __forceinline__ Split split_slots(int np, int vb, int nvb, int U) {
+__device__ __forceinline__ Split split_slots(int np, int vb, int nvb, int U, int num, int den) {
     Split s;
     s.nunits = (np + U - 1) / U;
-    const int per = (int)((long long)s.nunits * 7 / 8 / nvb);
+    const int per = (int)((long long)s.nunits * num / den / nvb);
     s.sbeg = (int)min((long long)vb * per * U, (long long)np);
     s.send = (int)min((long long)(vb + 1) * per * U, (long long)np);
     s.dyn0 = nvb * per;
@@ -724,7 +729,7 @@ template <> __device__ __forceinline__ void pass_a_body<float>(const SimDev<floa
         return;
     }
     constexpr int U = 2 * TPB;
-    const Split sp = split_slots(np, vb, nvb, U);
+    const Split sp = split_slots(np, vb, nvb, U, 15, 16);
     pass_a_range(S, P, geo, off, shift, seg, sp.sbeg, sp.send);
     for (;;) {
         const int u = next_unit(&S.d->ticket, sp.dyn0);
@@ -1093,7 +1098,7 @@ __device__ __forceinline__ void pass_b_body<float, false>(const SimDev<float> &S
         pass_b_range(S, P, geo, off, shift, snext, Q, wq, queued, rg.x, rg.y);
     } else {
         constexpr int U = 2 * TPB_B;
-        const Split sp = split_slots(np, vb, nvb, U);
+        const Split sp = split_slots(np, vb, nvb, U, 7, 8);
         pass_b_range(S, P, geo, off, shift, snext, Q, wq, queued, sp.sbeg, sp.send);
         for (;;) {
             const int u = next_unit(&S.d->ticket, sp.dyn0);
