@@ -185,7 +185,8 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
 // blocks of the SMs that finish their share early take more of the end.  With equal shares
 // only, the SMs' active cycles spread by 5-7 % of the launch (ncu sm__cycles_active min, avg,
 // max) and the launch lasted as long as the slowest.  Measured (3 alternating runs each): pass
-// A 0.0923 ms with equal shares, 0.0896 at 7/8, 0.0883 at 15/16, 0.092 at 3/4, 0.098 at 1/2;
+// A 0.0923 ms with equal shares, 0.0896 at 7/8, 0.0883 at 15/16, 0.0904 at 31/32, 0.092 at
+// 3/4, 0.098 at 1/2;
 // pass B 0.0925, 0.0905 at 7/8, 0.0945 at 15/16, 0.0915 at 3/4.  Each unit handed out costs
 // the ticket's round trip with the block waiting at a barrier; claiming the next unit one
 // iteration ahead (hiding that round trip) measured slower in pass B (spills) and within 0.5 %
