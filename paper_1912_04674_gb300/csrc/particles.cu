@@ -179,7 +179,7 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
     return q;
 }
 
-// Work split of the single-simulation FP32 passes: each block first takes a contiguous share
+// Work split of the single-simulation particle passes: each block first takes a contiguous share
 // of num/den of the slots, in units of U slots (one iteration of the block), then single units
 // of the rest from the descriptor's ticket counter (zeroed by the kernel before), so that the
 // blocks of the SMs that finish their share early take more of the end.  With equal shares
@@ -190,7 +190,8 @@ template <class R> __device__ __forceinline__ PReg<R> load_particle(const Parts<
 // pass B 0.0925, 0.0905 at 7/8, 0.0945 at 15/16, 0.0915 at 3/4.  Each unit handed out costs
 // the ticket's round trip with the block waiting at a barrier; claiming the next unit one
 // iteration ahead (hiding that round trip) measured slower in pass B (spills) and within 0.5 %
-// in pass A.
+// in pass A.  The one-particle-per-thread passes (FP64, and FP32 pass B with the charge change)
+// take 7/8.
 struct Split {
     int sbeg, send;   // the block's contiguous share
     int dyn0, nunits; // first unit handed out by ticket, number of units
@@ -335,27 +336,39 @@ template <class R> __device__ __forceinline__ void pass_a_body(const SimDev<R> &
     const Geo geo = S.geo;
     const int off = S.d->off, np = S.d->np;
     const long long shift = S.d->shift;
-    // each block walks one contiguous chunk of slots, so that its successive iterations
-    // gather from neighbouring cells (field lines stay in L1)
-    const int2 rg = slot_range(np, vb, nvb, csize);
-    const int begin = rg.x, end = rg.y;
-    int k = begin + threadIdx.x;
-    PReg<R> cur = load_particle<R>(P, k, end);
-    for (int base = begin; base < end; base += TPB, k += TPB) {
-        const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
-        const AOut<R> o = a_particle<R>(S, geo, off, shift, cur.ix, cur.ox, cur.y, cur.z, cur.px, cur.py,
-                                        cur.pz, cur.w);
-        if (cur.ix != kDead) {
-            P.px[k] = o.px;
-            P.py[k] = o.py;
-            P.pz[k] = o.pz;
+    // each block walks contiguous runs of slots, so that its successive iterations gather from
+    // neighbouring cells (field lines stay in L1)
+    auto range = [&](int begin, int end) {
+        int k = begin + threadIdx.x;
+        PReg<R> cur = load_particle<R>(P, k, end);
+        for (int base = begin; base < end; base += TPB, k += TPB) {
+            const PReg<R> nxt = load_particle<R>(P, k + TPB, end);   // prefetch
+            const AOut<R> o = a_particle<R>(S, geo, off, shift, cur.ix, cur.ox, cur.y, cur.z, cur.px, cur.py,
+                                            cur.pz, cur.w);
+            if (cur.ix != kDead) {
+                P.px[k] = o.px;
+                P.py[k] = o.py;
+                P.pz[k] = o.pz;
+            }
+            const Run run = run_of(o.key);
+            const R bnd[1] = {o.bnd};
+            double *const addr[4] = {S.f.chi + o.b, S.f.chi + o.b + geo.P, S.f.chi + o.b + 1,
+                                     S.f.chi + o.b + geo.P + 1};
+            run_deposit<1>(run, o.key, o.v, bnd, addr);
+            cur = nxt;
         }
-        const Run run = run_of(o.key);
-        const R bnd[1] = {o.bnd};
-        double *const addr[4] = {S.f.chi + o.b, S.f.chi + o.b + geo.P, S.f.chi + o.b + 1,
-                                 S.f.chi + o.b + geo.P + 1};
-        run_deposit<1>(run, o.key, o.v, bnd, addr);
-        cur = nxt;
+    };
+    if (csize > 0) {   // a work item of a fused launch
+        const int2 rg = slot_range(np, vb, nvb, csize);
+        range(rg.x, rg.y);
+        return;
+    }
+    const Split sp = split_slots(np, vb, nvb, TPB, 7, 8);   // the work split of the FP32 passes
+    range(sp.sbeg, sp.send);
+    for (;;) {
+        const int u = next_unit(&S.d->ticket, sp.dyn0);
+        if (u >= sp.nunits) break;
+        range(u * TPB, min(u * TPB + TPB, np));
     }
 }
 
@@ -940,34 +953,46 @@ template <class R, bool DQ> __device__ __forceinline__ void pass_b_body(const Si
     const int snext = window_shifts(S.ph, step, shift) ? 1 : 0;
     const int wq = threadIdx.x >> 5;
     int queued = 0;   // same value on every lane of the warp
-    // each block walks one contiguous chunk of slots (see pass A)
-    const int2 rg = slot_range(np, vb, nvb, csize);
-    const int begin = rg.x, end = rg.y;
-    int k = begin + threadIdx.x;
-    PReg<R> cur = load_particle<R>(P, k, end);
-    for (int base = begin; base < end; base += TPB_B, k += TPB_B) {
-        const PReg<R> nxt = load_particle<R>(P, k + TPB_B, end);   // prefetch
-        const BOut<R> o = b_particle<R>(S, geo, off, shift, snext, cur.ix, cur.ox, cur.y, cur.z, cur.px,
-                                        cur.py, cur.pz, cur.w);
-        enqueue_cross<R>(Q, wq, queued, o, cur.w);
-        latch_nonfinite(S.d, o.nonfinite);
-        const bool alive = cur.ix != kDead;
-        if (DQ && alive) charge_change<R>(S, geo, off, o, cur.w);
-        if (alive) {
-            P.ix[k] = o.ixn;
-            P.ox[k] = o.ox1;
-            P.y[k] = o.y1;
-            P.z[k] = o.z1;
+    // each block walks contiguous runs of slots (see pass A)
+    auto range = [&](int begin, int end) {
+        int k = begin + threadIdx.x;
+        PReg<R> cur = load_particle<R>(P, k, end);
+        for (int base = begin; base < end; base += TPB_B, k += TPB_B) {
+            const PReg<R> nxt = load_particle<R>(P, k + TPB_B, end);   // prefetch
+            const BOut<R> o = b_particle<R>(S, geo, off, shift, snext, cur.ix, cur.ox, cur.y, cur.z, cur.px,
+                                            cur.py, cur.pz, cur.w);
+            enqueue_cross<R>(Q, wq, queued, o, cur.w);
+            latch_nonfinite(S.d, o.nonfinite);
+            const bool alive = cur.ix != kDead;
+            if (DQ && alive) charge_change<R>(S, geo, off, o, cur.w);
+            if (alive) {
+                P.ix[k] = o.ixn;
+                P.ox[k] = o.ox1;
+                P.y[k] = o.y1;
+                P.z[k] = o.z1;
+            }
+            const Run run = run_of(o.key);
+            double *const addr[4] = {S.f.jx + o.b, S.f.jx + o.b + 1, S.f.jr + o.b, S.f.jr + o.b + geo.P};
+            run_deposit<2>(run, o.key, o.v, o.bnd, addr);
+            // at most 32 join per iteration, so draining at 32 keeps the queue within QW
+            if (queued >= 32) {
+                drain_queue<R>(S, off, Q, wq, queued);
+                queued = 0;
+            }
+            cur = nxt;
         }
-        const Run run = run_of(o.key);
-        double *const addr[4] = {S.f.jx + o.b, S.f.jx + o.b + 1, S.f.jr + o.b, S.f.jr + o.b + geo.P};
-        run_deposit<2>(run, o.key, o.v, o.bnd, addr);
-        // at most 32 join per iteration, so draining at 32 keeps the queue within QW
-        if (queued >= 32) {
-            drain_queue<R>(S, off, Q, wq, queued);
-            queued = 0;
+    };
+    if (csize > 0) {   // a work item of a fused launch
+        const int2 rg = slot_range(np, vb, nvb, csize);
+        range(rg.x, rg.y);
+    } else {
+        const Split sp = split_slots(np, vb, nvb, TPB_B, 7, 8);   // the work split of the FP32 passes
+        range(sp.sbeg, sp.send);
+        for (;;) {
+            const int u = next_unit(&S.d->ticket, sp.dyn0);
+            if (u >= sp.nunits) break;
+            range(u * TPB_B, min(u * TPB_B + TPB_B, np));
         }
-        cur = nxt;
     }
     drain_queue<R>(S, off, Q, wq, queued);
 }
