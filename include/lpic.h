@@ -179,7 +179,11 @@ lpic_status lpic_load_plasma(lpic_ctx *ctx, const lpic_plasma_params *plasma);
 /* Advance nsteps timesteps (paper Sec. 3, the 3D envelope loop order):
  * Faraday -> gather/chi deposit/ponderomotive Boris -> envelope solve (Eq. envelope_solver)
  * -> position push/charge-conserving current -> Ampere -> moving window/injection,
- * with a counting sort every sort_every steps.  Asynchronous on the context stream.
+ * with a counting sort every sort_every steps.  Asynchronous on the context stream.  The
+ * steps are replayed from CUDA graphs recorded on first use (eight steps per replay where none
+ * of them sorts or relocates the window, else one); with kernel timing on
+ * (lpic_set_kernel_timing) they are launched kernel by kernel instead.  The state reached is
+ * the same either way, up to the order of the FP64 atomic additions.
  * Conditions the kernels latch (plasma injection beyond the capacity: LPIC_EBUFSIZE; a
  * particle pushed to a non-finite position: LPIC_ENONFINITE) are returned by the next
  * lpic_step whose predecessor has completed, or by the next lpic_diagnose. */
