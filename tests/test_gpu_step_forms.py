@@ -9,9 +9,10 @@ additions (and, in FP32, in which block takes which slots), so their counters ag
 FP64 states agree with each other and with the oracle at the multi-step parity bar (1e-10 and
 1e-9; 6e-15 measured between forms), and FP32 states agree with each other at 1e-4: there the
 atomic order's last-bit differences in the fields flip FP32 roundings of single particles,
-which the following steps carry on (2.8e-6 measured, on chi, after 40 steps).  The grid (Nx = 24: 29 live columns in 58)
-makes the window relocate within the 40 steps, and the sort cadence of 11 leaves room for one
-eight-step replay after each sort, with single steps up to the next.
+which the following steps carry on (2.8e-6 measured, on chi, after 40 steps).  The grid
+(Nx = 24: 29 live columns in 58) makes the window relocate within the 40 steps, and the sort
+cadence of 11 leaves room for one eight-step replay after each sort, with single steps up to
+the next.
 """
 import dataclasses
 
